@@ -1,0 +1,251 @@
+/*
+ * lbpm.h - C ABI of the GB300 color-gradient lattice Boltzmann library.
+ *
+ * The library advances the two-fluid color-gradient LBM of the LBPM paper
+ * (arXiv 2007.12266) on the pore sites of a segmented 3-D image, on one
+ * NVIDIA GB300 (sm_103a). One context ("ctx") holds one simulated domain.
+ *
+ * Model (Sec. 3.1 "Color Lattice-Boltzmann Model"):
+ *   - D3Q19 MRT momentum LBE with body force F; equilibrium moments carry the
+ *     interfacial-tension terms alpha|C| (m1, m9, m11, m13, m14, m15),
+ *     sigma_ab = 6 alpha;
+ *   - two D3Q7 component distributions A, B recolored by the phase field
+ *     phi = (Na - Nb)/(Na + Nb) with parameter beta (Eqs. LBE-mass-a/b);
+ *   - wetting through a per-solid-voxel affinity phi_s that enters the
+ *     color gradient C (Sec. 3.2, Eq. phi_s: cos(theta_eq) = phi_s);
+ *   - streaming in place (AA pattern) with halfway bounce-back at solids.
+ *
+ * Conventions shared by every call:
+ *   - Voxel arrays are x-fastest: voxel (x, y, z) is at x + nx*(y + ny*z).
+ *   - Every host input buffer is owned by the caller and is copied before the
+ *     call returns; the library keeps no host pointer.
+ *   - Device memory is owned by the ctx. It comes from the allocator set with
+ *     lbpm_set_allocator (the Python binding installs PyTorch's caching
+ *     allocator), else from cudaMalloc.
+ *   - Work is issued on the ctx's CUDA stream. Calls that return host data
+ *     synchronize that stream; lbpm_advance does not.
+ *   - No C++ exception crosses this ABI. Every call returns an lbpm_status;
+ *     lbpm_last_error(ctx) gives a message for the last failure. Errors raised
+ *     asynchronously by device work surface at the next lbpm_sync,
+ *     lbpm_measure, lbpm_read_* or lbpm_advance call.
+ *   - A ctx is not thread-safe: use it from one host thread at a time.
+ */
+#ifndef LBPM_H
+#define LBPM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbpm_ctx lbpm_ctx;
+
+typedef enum {
+    LBPM_OK = 0,
+    LBPM_E_INVALID = 1,   /* bad argument, size or parameter */
+    LBPM_E_OOM = 2,       /* device allocation failed */
+    LBPM_E_CUDA = 3,      /* a CUDA runtime call or kernel launch failed */
+    LBPM_E_STATE = 4,     /* call out of order (e.g. advance before init) */
+    LBPM_E_UNSTABLE = 5,  /* the last measure found non-finite or negative densities */
+    LBPM_E_TIMEOUT = 6    /* a bounded device-side wait gave up */
+} lbpm_status;
+
+/* Storage precision of the distributions. */
+enum { LBPM_FP32 = 0, LBPM_FP16 = 1 };
+
+/* Field selectors for lbpm_read_field. */
+enum { LBPM_FIELD_PHI = 0, LBPM_FIELD_PRESSURE = 1, LBPM_FIELD_UX = 2,
+       LBPM_FIELD_UY = 3, LBPM_FIELD_UZ = 4, LBPM_FIELD_NA = 5, LBPM_FIELD_NB = 6,
+       LBPM_FIELD_RHO = 7 };
+
+/* Distribution selectors for lbpm_read_distributions / lbpm_write_distributions. */
+enum { LBPM_DIST_F = 0, LBPM_DIST_A = 1, LBPM_DIST_B = 2 };
+
+/*
+ * Model parameters (Sec. 3.1): tau_a, tau_b set the kinematic viscosity of
+ * each fluid, nu = (tau - 1/2)/3 (the relaxation matrix "is determined based
+ * on the kinematic viscosity"); alpha sets the interfacial tension
+ * sigma_ab = 6 alpha; beta sets the interface thickness; force is the
+ * constant body force F. Unsteady-flow reservoirs (Sec. 4.1): with
+ * reservoir_z = 1 the four z-layers at z = 0 hold fluid A at density rho_in
+ * and the four at z = nz - 1 hold fluid B at rho_out; the z axis must then be
+ * non-periodic.
+ * Valid ranges: tau > 0.5; alpha >= 0; beta >= 0 (0 disables recoloring);
+ * finite force; precision LBPM_FP32 or LBPM_FP16; periodic[i] in {0, 1};
+ * rho_in, rho_out > 0. Otherwise LBPM_E_INVALID.
+ */
+typedef struct {
+    double tau_a, tau_b;
+    double alpha, beta;
+    double force[3];
+    int precision;
+    int periodic[3];      /* 1 = periodic axis; a non-periodic face is a solid wall (phi_s = 0) */
+    int reservoir_z;
+    double rho_in, rho_out;
+} lbpm_params;
+
+/*
+ * Basic analysis and integral measures of the current state, all summed in
+ * fp64 on the device in a fixed order (deterministic for a given domain):
+ * basic analysis of Sec. 4 (saturation, average velocity and pressure per
+ * fluid, instability detection) and the integral measures of Sec. 3.4 (table
+ * of integral measures: M, P, K per fluid region, p_alpha = mean pressure;
+ * regions: phi > 0 is fluid A, the rest is B). Velocities are the reported
+ * velocity u = (j + F/2)/rho0, pressure p = rho/3.
+ *   sat_mass   = sum Na / sum (Na + Nb)         (conserved saturation of A)
+ *   sat_count  = #{phi > 0} / n_sites
+ *   flux       = (1/V) sum_pore u  (Darcy flux; V counts all voxels)
+ *   flux_a/b   = (1/V) sum_pore (Na/N) u, (Nb/N) u
+ *   mom_a/b    = sum_region rho u; ke_a/b = sum_region rho u.u
+ *   mass_a/b   = sum Na, sum Nb; mass_total = sum rho
+ *   vol_a/b    = site counts of the regions; p_a/b = region mean of p
+ *   ca         = total capillary number, Eq. capillary_number:
+ *                (eps_a mu_a |<u>_a| + eps_b mu_b |<u>_b|)/sigma with
+ *                <u>_alpha = P_alpha/M_alpha, eps_alpha = vol_alpha/V,
+ *                mu = (tau - 1/2)/3, sigma = 6 alpha
+ *   status     = 0 ok, bit 0 non-finite value, bit 1 negative component density
+ */
+typedef struct {
+    long long step;
+    double sat_mass, sat_count;
+    double mass_a, mass_b, mass_total;
+    double mom_a[3], mom_b[3];
+    double flux[3], flux_a[3], flux_b[3];
+    double ke_a, ke_b;
+    double p_a, p_b;
+    double vol_a, vol_b;
+    double ca;
+    long long n_sites;
+    int status;
+} lbpm_measures;
+
+/* Device allocator hooks: alloc returns a device pointer of at least `bytes`
+ * usable on `stream`, or NULL; free releases it. `user` is passed back. */
+typedef void* (*lbpm_alloc_fn)(size_t bytes, void* stream, void* user);
+typedef void (*lbpm_free_fn)(void* ptr, void* user);
+
+/* Library version string (static storage). */
+const char* lbpm_version(void);
+
+/* Create a ctx on CUDA `device`, issuing work on `cuda_stream` (a
+ * cudaStream_t; NULL = the legacy default stream). *out receives the ctx.
+ * Errors: LBPM_E_INVALID (out NULL, bad device), LBPM_E_CUDA. */
+lbpm_status lbpm_create(lbpm_ctx** out, int device, void* cuda_stream);
+
+/* Free every device buffer of the ctx and the ctx itself. NULL is a no-op. */
+lbpm_status lbpm_destroy(lbpm_ctx* ctx);
+
+/* Route the ctx's device allocations through alloc/free. Must be called
+ * before lbpm_load_image (LBPM_E_STATE otherwise). NULL alloc restores
+ * cudaMalloc/cudaFree. */
+lbpm_status lbpm_set_allocator(lbpm_ctx* ctx, lbpm_alloc_fn alloc, lbpm_free_fn free_fn,
+                               void* user);
+
+/* Message for the last failed call on ctx (or the last failed lbpm_create
+ * when ctx is NULL). Valid until the next call on the ctx. */
+const char* lbpm_last_error(const lbpm_ctx* ctx);
+
+/*
+ * Load the labelled image (Sec. 3.3, "Initial conditions and wetting maps":
+ * one integer label per voxel). labels: uint16 [nz][ny][nx], x fastest;
+ * label 0 = pore, label k >= 1 = solid of wetting class k. Builds the sparse
+ * pore-site index on the device: pore voxels are numbered in x-fastest
+ * lexicographic order, and each site's 18 neighbours are resolved with
+ * periodic wrap on the axes params.periodic marks (call lbpm_set_params
+ * first, or the default is periodic on all axes). Affinities default to 0
+ * until lbpm_set_affinity_* is called. Replaces any previous image and
+ * discards the fluid state.
+ * Limits: nx, ny, nz >= 1; (nx+2)(ny+2)(nz+2) < 2^31; at least one pore.
+ * Errors: LBPM_E_INVALID, LBPM_E_OOM, LBPM_E_CUDA.
+ */
+lbpm_status lbpm_load_image(lbpm_ctx* ctx, const uint16_t* labels, int nx, int ny, int nz);
+
+/* Wetting map by label (Sec. 3.2: "the wetting map assigns a label to each
+ * solid voxel, and the associated wetting affinity is specified for each
+ * label"): affinity_by_label[k] is phi_s of label k, for k < n_labels
+ * (entry 0 is ignored). Labels >= n_labels get 0. |phi_s| <= 1.
+ * Requires a loaded image (LBPM_E_STATE). Takes effect from the next step. */
+lbpm_status lbpm_set_affinity_table(lbpm_ctx* ctx, const float* affinity_by_label, int n_labels);
+
+/* Per-voxel wetting map: affinity_per_voxel float [nz][ny][nx]; values at
+ * solid voxels are used as phi_s, pore entries are ignored. |phi_s| <= 1. */
+lbpm_status lbpm_set_affinity_map(lbpm_ctx* ctx, const float* affinity_per_voxel);
+
+/* Set the model parameters (see lbpm_params). Periodicity and precision
+ * changes after lbpm_load_image rebuild the index / storage and discard the
+ * fluid state (LBPM_E_STATE is not raised; the state must be re-initialised). */
+lbpm_status lbpm_set_params(lbpm_ctx* ctx, const lbpm_params* params);
+
+/* Initialise the fluids from a phase field phi0 float [nz][ny][nx] (pore
+ * entries read, clamped to [-1, 1]): Na = (1+phi0)/2, Nb = (1-phi0)/2,
+ * A_q = w_q Na, B_q = w_q Nb, f_q = t_q (rho = 1, u = 0); step counter 0.
+ * Reservoir layers, if enabled, are then set. Errors: LBPM_E_STATE (no image). */
+lbpm_status lbpm_init_fluids(lbpm_ctx* ctx, const float* phi0_per_voxel);
+
+/* Enqueue nsteps timesteps on the ctx stream (asynchronous). Each step: the
+ * phase pass (phi and N from A, B), then the fused collide-stream pass
+ * (color gradient, MRT collision with the alpha terms and the force,
+ * recoloring, AA streaming with bounce-back), then the reservoir reset.
+ * nsteps >= 0. Errors: LBPM_E_STATE (no fluids), LBPM_E_UNSTABLE (a previous
+ * measure flagged the state), LBPM_E_CUDA. */
+lbpm_status lbpm_advance(lbpm_ctx* ctx, long long nsteps);
+
+/* Wait for the ctx stream and report any asynchronous device error. */
+lbpm_status lbpm_sync(lbpm_ctx* ctx);
+
+/* Compute the measures of the current state (synchronizes). Returns
+ * LBPM_E_UNSTABLE, with *out filled, when out->status != 0. */
+lbpm_status lbpm_measure(lbpm_ctx* ctx, lbpm_measures* out);
+
+/* Dense field of the current state into out_dense float [nz][ny][nx]
+ * (caller-allocated, nx*ny*nz floats); solid voxels get NaN. */
+lbpm_status lbpm_read_field(lbpm_ctx* ctx, int which, float* out_dense);
+
+/* Distributions of the current state in canonical order, population-major:
+ * out[q*n_sites + n] = f_q (or A_q, B_q) at site n, the value the next step
+ * will collide, whatever the AA parity. Q = 19 for F, 7 for A, B. */
+lbpm_status lbpm_read_distributions(lbpm_ctx* ctx, int which, float* out_canonical);
+
+/* Overwrite one distribution set from canonical order (same layout as
+ * lbpm_read_distributions) at the current step parity. */
+lbpm_status lbpm_write_distributions(lbpm_ctx* ctx, int which, const float* in_canonical);
+
+/* Number of pore sites of the loaded image (0 before lbpm_load_image). */
+lbpm_status lbpm_num_sites(const lbpm_ctx* ctx, long long* n_sites);
+
+/* Completed timesteps since lbpm_init_fluids / lbpm_restore. */
+lbpm_status lbpm_step_count(const lbpm_ctx* ctx, long long* step);
+
+/* The sparse index: site2vox int64 [n_sites] (voxel index of each site) and
+ * nbr int32 [18][n_sites]: nbr[(q-1)*n_sites + n] is the site reached from
+ * site n along xi_q (q = 1..18, D3Q19 order of Eq. d3q19 with the sign order
+ * (+,-) per axis pair and (++, --, +-, -+) per edge group), wrapped on
+ * periodic axes, or -1 where that voxel is solid or outside the domain.
+ * Either pointer may be NULL to skip it. */
+lbpm_status lbpm_get_index(lbpm_ctx* ctx, int64_t* site2vox, int32_t* nbr);
+
+/* Snapshot of the full fluid state (distributions in canonical fp32 order
+ * plus the step counter) into host_buf. With host_buf NULL, *bytes receives
+ * the size needed. lbpm_restore reloads such a snapshot into a ctx holding
+ * the same image; the next steps are bit-identical to an uninterrupted run
+ * in FP32 storage. Errors: LBPM_E_INVALID (size or header mismatch). */
+lbpm_status lbpm_snapshot(lbpm_ctx* ctx, void* host_buf, size_t* bytes);
+lbpm_status lbpm_restore(lbpm_ctx* ctx, const void* host_buf, size_t bytes);
+
+/* Kernel timing for roofline reports: while enabled, lbpm_advance records CUDA
+ * events around each launch of the fused collide-stream kernel on the ctx
+ * stream. lbpm_kernel_timing returns (after synchronizing) the summed event
+ * time in ms and the launch count since the last reset, and resets them. */
+lbpm_status lbpm_enable_kernel_timing(lbpm_ctx* ctx, int enable);
+lbpm_status lbpm_kernel_timing(lbpm_ctx* ctx, double* ms_collide, long long* n_collide,
+                               double* ms_phase, long long* n_phase);
+
+/* Number of kernel launches issued by this ctx since creation. */
+lbpm_status lbpm_launch_count(const lbpm_ctx* ctx, long long* launches);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBPM_H */

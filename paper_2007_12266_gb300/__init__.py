@@ -1,0 +1,260 @@
+"""GB300-native color-gradient lattice Boltzmann (LBPM two-fluid model).
+
+Python binding of the CUDA library ``libcolorlbm.so`` (C ABI in
+``include/lbpm.h``). This layer only marshals arguments: image loading,
+indexing, time stepping, measures and exports all run in the library's CUDA
+kernels on sm_103a. PyTorch supplies the device memory (its caching
+allocator) and the CUDA stream.
+
+Model: Sec. 3.1 of the LBPM paper (arXiv 2007.12266) - D3Q19 MRT momentum
+LBE with the color-gradient interfacial-tension terms, two D3Q7 component
+LBEs with recoloring, wetting affinity phi_s at solid voxels (Sec. 3.2).
+"""
+from __future__ import annotations
+
+import atexit
+import ctypes as ct
+import weakref
+from typing import Optional
+
+import numpy as np
+
+from . import _lib
+from ._lib import LBPMError, Measures, Params
+
+__all__ = ["Domain", "LBPMError", "FIELDS", "DISTS", "library_path", "version"]
+
+FIELDS = {"phi": 0, "pressure": 1, "ux": 2, "uy": 3, "uz": 4, "na": 5, "nb": 6, "rho": 7}
+DISTS = {"f": (0, 19), "a": (1, 7), "b": (2, 7)}
+PRECISION = {"fp32": 0, "fp16": 1}
+
+
+def library_path() -> str:
+    return _lib.library_path()
+
+
+def version() -> str:
+    return _lib.load().lbpm_version().decode()
+
+
+_LIVE = weakref.WeakSet()
+
+
+@atexit.register
+def _close_all():
+    # release device memory through the allocator callbacks while torch is alive
+    for d in list(_LIVE):
+        try:
+            d.close()
+        except Exception:
+            pass
+
+
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        raise RuntimeError("no CUDA device: the color-LBM library runs on the GPU only")
+    return torch
+
+
+class Domain:
+    """One simulated domain (one library context) on one GPU.
+
+    labels   : uint16 array (nz, ny, nx), 0 = pore, k >= 1 = solid of wetting class k
+    affinity : optional float32 (nz, ny, nx) per-voxel phi_s (solid voxels read)
+    periodic : (px, py, pz) flags; non-periodic faces are solid walls
+    precision: "fp32" or "fp16" storage of the distributions
+    """
+
+    def __init__(self, labels: np.ndarray, affinity: Optional[np.ndarray] = None, *,
+                 periodic=(1, 1, 1), tau_a=0.7, tau_b=0.7, alpha=0.005, beta=0.95,
+                 force=(0.0, 0.0, 0.0), precision="fp32", reservoir_z=0, rho_in=1.0,
+                 rho_out=1.0, device: int = 0, stream=None, use_torch_allocator: bool = True):
+        torch = _torch()
+        self._L = _lib.load()
+        self.device = int(device)
+        with torch.cuda.device(self.device):
+            self._stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        h = ct.c_void_p()
+        st = self._L.lbpm_create(ct.byref(h), self.device, ct.c_void_p(self._stream.cuda_stream))
+        if st != 0:
+            raise LBPMError(st, self._L.lbpm_last_error(None).decode())
+        self._h = h
+        _LIVE.add(self)
+        self._callbacks = None
+        if use_torch_allocator:
+            dev, strm = self.device, self._stream
+
+            def _alloc(nbytes, stream, user):
+                try:
+                    return int(torch.cuda.caching_allocator_alloc(int(nbytes), dev, strm))
+                except Exception:
+                    return None
+
+            def _free(ptr, user):
+                try:
+                    torch.cuda.caching_allocator_delete(int(ptr))
+                except Exception:
+                    pass
+
+            self._callbacks = (_lib.ALLOC_FN(_alloc), _lib.FREE_FN(_free))
+            self._check(self._L.lbpm_set_allocator(self._h, self._callbacks[0], self._callbacks[1], None))
+        self.set_params(tau_a=tau_a, tau_b=tau_b, alpha=alpha, beta=beta, force=force,
+                        precision=precision, periodic=periodic, reservoir_z=reservoir_z,
+                        rho_in=rho_in, rho_out=rho_out)
+        self.load_image(labels)
+        if affinity is not None:
+            self.set_affinity_map(affinity)
+
+    # -- plumbing --------------------------------------------------------
+    def _check(self, status: int):
+        if status != 0:
+            raise LBPMError(status, self._L.lbpm_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._L.lbpm_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- setup -----------------------------------------------------------
+    def load_image(self, labels: np.ndarray):
+        """(Re)load the labelled image and rebuild the pore-site index; the
+        fluid state must then be initialised again."""
+        labels = np.ascontiguousarray(labels, dtype=np.uint16)
+        if labels.ndim != 3:
+            raise ValueError("labels must be a 3-D (nz, ny, nx) array")
+        nz, ny, nx = labels.shape
+        self._check(self._L.lbpm_load_image(self._h, labels.ctypes.data, nx, ny, nz))
+        self.shape = labels.shape
+
+    def set_params(self, *, tau_a, tau_b, alpha, beta, force, precision="fp32",
+                   periodic=(1, 1, 1), reservoir_z=0, rho_in=1.0, rho_out=1.0):
+        p = Params()
+        p.tau_a, p.tau_b, p.alpha, p.beta = float(tau_a), float(tau_b), float(alpha), float(beta)
+        for a in range(3):
+            p.force[a] = float(force[a])
+            p.periodic[a] = int(periodic[a])
+        p.precision = PRECISION[precision] if isinstance(precision, str) else int(precision)
+        p.reservoir_z = int(reservoir_z)
+        p.rho_in, p.rho_out = float(rho_in), float(rho_out)
+        self._check(self._L.lbpm_set_params(self._h, ct.byref(p)))
+        self.params = dict(tau_a=tau_a, tau_b=tau_b, alpha=alpha, beta=beta, force=tuple(force),
+                           precision=precision, periodic=tuple(periodic), reservoir_z=reservoir_z,
+                           rho_in=rho_in, rho_out=rho_out)
+
+    def update_params(self, **kw):
+        p = dict(self.params)
+        p.update(kw)
+        self.set_params(**p)
+
+    def set_affinity_map(self, affinity: np.ndarray):
+        a = np.ascontiguousarray(affinity, dtype=np.float32)
+        if a.shape != self.shape:
+            raise ValueError("affinity map must match the image shape")
+        self._check(self._L.lbpm_set_affinity_map(self._h, a.ctypes.data))
+
+    def set_affinity_table(self, table):
+        t = np.ascontiguousarray(table, dtype=np.float32)
+        self._check(self._L.lbpm_set_affinity_table(self._h, t.ctypes.data, int(t.size)))
+
+    def init_fluids(self, phi0: np.ndarray):
+        p = np.ascontiguousarray(phi0, dtype=np.float32)
+        if p.shape != self.shape:
+            raise ValueError("phi0 must match the image shape")
+        self._check(self._L.lbpm_init_fluids(self._h, p.ctypes.data))
+
+    # -- running ---------------------------------------------------------
+    def advance(self, nsteps: int):
+        self._check(self._L.lbpm_advance(self._h, int(nsteps)))
+
+    def sync(self):
+        self._check(self._L.lbpm_sync(self._h))
+
+    def measure(self, raise_unstable: bool = False) -> dict:
+        m = Measures()
+        st = self._L.lbpm_measure(self._h, ct.byref(m))
+        if st != 0 and (st != 5 or raise_unstable):
+            self._check(st)
+        out = {}
+        for name, _ in Measures._fields_:
+            v = getattr(m, name)
+            out[name] = list(v) if hasattr(v, "__len__") else v
+        return out
+
+    # -- results ---------------------------------------------------------
+    @property
+    def n_sites(self) -> int:
+        n = ct.c_longlong()
+        self._check(self._L.lbpm_num_sites(self._h, ct.byref(n)))
+        return n.value
+
+    @property
+    def step_count(self) -> int:
+        n = ct.c_longlong()
+        self._check(self._L.lbpm_step_count(self._h, ct.byref(n)))
+        return n.value
+
+    @property
+    def launch_count(self) -> int:
+        n = ct.c_longlong()
+        self._check(self._L.lbpm_launch_count(self._h, ct.byref(n)))
+        return n.value
+
+    def read_field(self, name: str) -> np.ndarray:
+        out = np.empty(self.shape, dtype=np.float32)
+        self._check(self._L.lbpm_read_field(self._h, FIELDS[name], out.ctypes.data))
+        return out
+
+    def distributions(self, which: str) -> np.ndarray:
+        code, Q = DISTS[which]
+        out = np.empty((Q, self.n_sites), dtype=np.float32)
+        self._check(self._L.lbpm_read_distributions(self._h, code, out.ctypes.data))
+        return out
+
+    def write_distributions(self, which: str, values: np.ndarray):
+        code, Q = DISTS[which]
+        v = np.ascontiguousarray(values, dtype=np.float32)
+        if v.shape != (Q, self.n_sites):
+            raise ValueError(f"expected shape {(Q, self.n_sites)}")
+        self._check(self._L.lbpm_write_distributions(self._h, code, v.ctypes.data))
+
+    def index(self):
+        N = self.n_sites
+        sv = np.empty(N, dtype=np.int64)
+        nb = np.empty((18, N), dtype=np.int32)
+        self._check(self._L.lbpm_get_index(self._h, sv.ctypes.data, nb.ctypes.data))
+        return sv, nb
+
+    def snapshot(self) -> bytes:
+        n = ct.c_size_t(0)
+        self._check(self._L.lbpm_snapshot(self._h, None, ct.byref(n)))
+        buf = ct.create_string_buffer(n.value)
+        self._check(self._L.lbpm_snapshot(self._h, buf, ct.byref(n)))
+        return buf.raw[: n.value]
+
+    def restore(self, snap: bytes):
+        buf = ct.create_string_buffer(snap, len(snap))
+        self._check(self._L.lbpm_restore(self._h, buf, len(snap)))
+
+    # -- timing ----------------------------------------------------------
+    def enable_kernel_timing(self, on: bool = True):
+        self._check(self._L.lbpm_enable_kernel_timing(self._h, int(bool(on))))
+
+    def kernel_timing(self) -> dict:
+        mc, nc, mp, np_ = ct.c_double(), ct.c_longlong(), ct.c_double(), ct.c_longlong()
+        self._check(self._L.lbpm_kernel_timing(self._h, ct.byref(mc), ct.byref(nc), ct.byref(mp),
+                                               ct.byref(np_)))
+        return {"collide_ms": mc.value, "collide_launches": nc.value,
+                "phase_ms": mp.value, "phase_launches": np_.value}

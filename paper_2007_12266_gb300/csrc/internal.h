@@ -1,0 +1,118 @@
+// Host-side context and the device view shared by the CUDA translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/lbpm.h"
+
+namespace lbm {
+
+// Everything a step kernel needs, passed by value as a kernel parameter.
+// Grids are "padded": (nx+2)(ny+2)(nz+2) voxels, one halo layer per face, so
+// neighbour voxel = v + off[q] never leaves the allocation. The halo of a
+// periodic axis mirrors the opposite face; on a non-periodic axis it is wall.
+struct DomainView {
+    int n_sites;        // N: pore sites
+    int n_halo;         // H: halo voxels that mirror a pore site
+    int off[19];        // padded-grid offset of xi_q
+    const int* site_vox;   // [N] padded voxel of each site
+    const int* vsite;      // [Vp] site id, -1 for solid / wall
+    float* phi;            // [Vp] phase field; solids hold phi_s, walls 0
+    const int* halo_dst;   // [H] padded halo voxel
+    const int* halo_site;  // [H] site it mirrors
+    float* nsum;           // [N] Na + Nb of the current step (phase pass -> collision)
+    void* f;               // [19][N] momentum distributions (AA in place)
+    void* a;               // [7][N]  component A
+    void* b;               // [7][N]  component B
+    float tau_a, tau_b, alpha, beta;
+    float fx, fy, fz;
+    float s_nu, s_m;       // rates when tau_a == tau_b
+    int uniform_tau;
+};
+
+struct Allocation {
+    void* ptr;
+    size_t bytes;
+};
+
+}  // namespace lbm
+
+struct lbpm_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    std::string err;
+    // allocator
+    lbpm_alloc_fn alloc = nullptr;
+    lbpm_free_fn free_fn = nullptr;
+    void* alloc_user = nullptr;
+    std::vector<lbm::Allocation> allocs;
+    // image
+    int nx = 0, ny = 0, nz = 0;
+    int px = 0, py = 0, pz = 0;
+    long long V = 0, Vp = 0;
+    long long N = 0, H = 0;
+    bool have_image = false, have_fluids = false, unstable = false;
+    uint16_t* d_labels = nullptr;   // [V]
+    int* d_site_vox = nullptr;      // [N]
+    int* d_vsite = nullptr;         // [Vp]
+    float* d_phi = nullptr;         // [Vp]
+    int* d_halo_dst = nullptr;      // [H]
+    int* d_halo_site = nullptr;     // [H]
+    float* d_nsum = nullptr;        // [N]
+    void* d_f = nullptr;
+    void* d_a = nullptr;
+    void* d_b = nullptr;
+    int* d_slab_site = nullptr;     // reservoir sites
+    signed char* d_slab_side = nullptr;
+    long long n_slab = 0;
+    double* d_partials = nullptr;   // measure partial sums
+    long long n_partials = 0;
+    // parameters and state
+    lbpm_params params{};
+    long long step = 0;
+    long long launches = 0;
+    int block = 256;
+    // kernel timing
+    bool timing = false;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<std::pair<int, int>> ev_collide, ev_phase;  // (start, end) indices
+    size_t ev_next = 0;
+};
+
+namespace lbm {
+
+// device memory through the ctx's allocator
+void* dalloc(lbpm_ctx* c, size_t bytes);
+void dfree(lbpm_ctx* c, void* p);
+
+// launchers (return cudaError_t of the launch)
+cudaError_t launch_flag_pore(const uint16_t* labels, long long V, int* flags, cudaStream_t s);
+cudaError_t exclusive_scan(lbpm_ctx* c, const int* in, int* out, long long n);
+cudaError_t launch_scatter_sites(const lbpm_ctx* c, const int* scan, cudaStream_t s);
+cudaError_t launch_fill_halo(const lbpm_ctx* c, cudaStream_t s);
+cudaError_t launch_halo_flags(const lbpm_ctx* c, int* flags, cudaStream_t s);
+cudaError_t launch_halo_scatter(const lbpm_ctx* c, const int* flags, const int* scan, cudaStream_t s);
+cudaError_t launch_affinity_table(const lbpm_ctx* c, const float* table, int n_labels, cudaStream_t s);
+cudaError_t launch_affinity_map(const lbpm_ctx* c, const float* map, cudaStream_t s);
+cudaError_t launch_slab_flags(const lbpm_ctx* c, int* flags, cudaStream_t s);
+cudaError_t launch_slab_scatter(const lbpm_ctx* c, const int* flags, const int* scan, cudaStream_t s);
+cudaError_t launch_export_index(const lbpm_ctx* c, long long* site2vox, int* nbr, cudaStream_t s);
+
+DomainView make_view(const lbpm_ctx* c);
+cudaError_t launch_init_fluids(const lbpm_ctx* c, const float* phi0, cudaStream_t s);
+cudaError_t launch_phase(const lbpm_ctx* c, int parity, cudaStream_t s);
+cudaError_t launch_collide(const lbpm_ctx* c, int parity, cudaStream_t s);
+cudaError_t launch_reservoir(const lbpm_ctx* c, int parity, cudaStream_t s);
+
+constexpr int NSUM = 27;  // per-site sums reduced by the measure kernel
+cudaError_t launch_measure(lbpm_ctx* c, int parity, double* d_out, cudaStream_t s);
+cudaError_t launch_field(const lbpm_ctx* c, int parity, int which, float* dense, cudaStream_t s);
+cudaError_t launch_export_dist(const lbpm_ctx* c, int parity, int which, float* out, cudaStream_t s);
+cudaError_t launch_import_dist(const lbpm_ctx* c, int parity, int which, const float* in, cudaStream_t s);
+
+}  // namespace lbm

@@ -1,0 +1,301 @@
+// Basic analysis and integral measures (Sec. 3.4 table of integral measures;
+// Sec. 4 basic analysis: saturation, velocity and pressure per fluid, and the
+// instability check), field export and distribution import/export.
+//
+// The reductions accumulate in fp64 in a fixed order: each thread walks a
+// fixed strided set of sites, blocks reduce with warp shuffles and shared
+// memory, and one block reduces the per-block partials. The result depends
+// only on the domain, never on timing.
+#include <limits>
+
+#include "step_kernels.cuh"
+
+namespace lbm {
+
+namespace {
+
+constexpr int kBlock = 256;
+constexpr int kMeasureBlocks = 152 * 4;
+
+inline unsigned blocks_for(long long n) { return static_cast<unsigned>((n + kBlock - 1) / kBlock); }
+
+// Current-state populations of site n at AA parity PAR (the values the next
+// step collides), in canonical order.
+template <int PAR, class S>
+__device__ __forceinline__ void load_site(const DomainView& d, int n, float (&f)[Q19], float (&a)[Q7],
+                                          float (&b)[Q7]) {
+    const int v = d.site_vox[n];
+    int nb[Q19];
+    if constexpr (PAR == 1) {
+        static_for<1, Q19>([&](auto qc) {
+            constexpr int q = decltype(qc)::value;
+            nb[q] = __ldg(d.vsite + v + d.off[q]);
+        });
+    }
+    static_for<0, Q19>([&](auto qc) {
+        constexpr int q = decltype(qc)::value;
+        const size_t i = read_slot<PAR, q>(d, n, nb);
+        f[q] = S::template ld_f<q>(d.f, i);
+        if constexpr (q < Q7) {
+            a[q] = S::template ld_c<q>(d.a, i);
+            b[q] = S::template ld_c<q>(d.b, i);
+        }
+    });
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Sum layout (NSUM = 27):
+//  0 Na, 1 Nb, 2 rho, 3 #(phi > 0), 4-6 u, 7-9 (Na/N) u, 10-12 (Nb/N) u,
+//  13 M_a, 14 M_b, 15-17 P_a, 18-20 P_b, 21 K_a, 22 K_b, 23 p over A,
+//  24 p over B, 25 #non-finite, 26 #negative component density
+template <int PAR, class S>
+__global__ void __launch_bounds__(kBlock) k_measure(DomainView d, double* partials) {
+    double acc[NSUM];
+#pragma unroll
+    for (int i = 0; i < NSUM; ++i) acc[i] = 0.0;
+    const float hfx = 0.5f * d.fx, hfy = 0.5f * d.fy, hfz = 0.5f * d.fz;
+    for (int n = blockIdx.x * kBlock + threadIdx.x; n < d.n_sites; n += gridDim.x * kBlock) {
+        float f[Q19], a[Q7], b[Q7];
+        load_site<PAR, S>(d, n, f, a, b);
+        double Na = 0.0, Nb = 0.0, rho = 0.0, jx = 0.0, jy = 0.0, jz = 0.0;
+        bool finite = true;
+        static_for<0, Q19>([&](auto qc) {
+            constexpr int q = decltype(qc)::value;
+            const double v = f[q];
+            finite = finite && isfinite(f[q]);
+            rho += v;
+            if constexpr (cx(q) != 0) jx += cx(q) * v;
+            if constexpr (cy(q) != 0) jy += cy(q) * v;
+            if constexpr (cz(q) != 0) jz += cz(q) * v;
+            if constexpr (q < Q7) {
+                Na += a[q];
+                Nb += b[q];
+            }
+        });
+        finite = finite && isfinite(Na) && isfinite(Nb);
+        const double Nt = Na + Nb;
+        const double phi = Nt > 0.0 ? (Na - Nb) / Nt : 0.0;
+        const double ux = jx + hfx, uy = jy + hfy, uz = jz + hfz;
+        const double uu = ux * ux + uy * uy + uz * uz;
+        const double p = rho / 3.0;
+        const double xa = Nt > 0.0 ? Na / Nt : 0.0, xb = Nt > 0.0 ? Nb / Nt : 0.0;
+        acc[0] += Na;
+        acc[1] += Nb;
+        acc[2] += rho;
+        acc[4] += ux;
+        acc[5] += uy;
+        acc[6] += uz;
+        acc[7] += xa * ux;
+        acc[8] += xa * uy;
+        acc[9] += xa * uz;
+        acc[10] += xb * ux;
+        acc[11] += xb * uy;
+        acc[12] += xb * uz;
+        if (phi > 0.0) {
+            acc[3] += 1.0;
+            acc[13] += rho;
+            acc[15] += rho * ux;
+            acc[16] += rho * uy;
+            acc[17] += rho * uz;
+            acc[21] += rho * uu;
+            acc[23] += p;
+        } else {
+            acc[14] += rho;
+            acc[18] += rho * ux;
+            acc[19] += rho * uy;
+            acc[20] += rho * uz;
+            acc[22] += rho * uu;
+            acc[24] += p;
+        }
+        if (!finite) acc[25] += 1.0;
+        if (Na < -1e-6 || Nb < -1e-6) acc[26] += 1.0;
+    }
+    __shared__ double red[kBlock / 32][NSUM];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int i = 0; i < NSUM; ++i) {
+        const double s = warp_sum(acc[i]);
+        if (lane == 0) red[w][i] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x < NSUM) {
+        double s = 0.0;
+        for (int k = 0; k < kBlock / 32; ++k) s += red[k][threadIdx.x];
+        partials[static_cast<size_t>(blockIdx.x) * NSUM + threadIdx.x] = s;
+    }
+}
+
+__global__ void k_reduce_partials(const double* partials, int nblocks, double* out) {
+    const int i = threadIdx.x;
+    if (i >= NSUM) return;
+    double s = 0.0;
+    for (int k = 0; k < nblocks; ++k) s += partials[static_cast<size_t>(k) * NSUM + i];
+    out[i] = s;
+}
+
+__global__ void k_fill(float* p, long long n, float v) {
+    const long long i = static_cast<long long>(blockIdx.x) * kBlock + threadIdx.x;
+    if (i < n) p[i] = v;
+}
+
+template <int PAR, class S>
+__global__ void __launch_bounds__(kBlock) k_field(DomainView d, int which, int nx, int ny, int px,
+                                                  int py, float* dense) {
+    const int n = blockIdx.x * kBlock + threadIdx.x;
+    if (n >= d.n_sites) return;
+    float f[Q19], a[Q7], b[Q7];
+    load_site<PAR, S>(d, n, f, a, b);
+    float Na = 0.0f, Nb = 0.0f, rho = 0.0f, jx = 0.0f, jy = 0.0f, jz = 0.0f;
+    static_for<0, Q19>([&](auto qc) {
+        constexpr int q = decltype(qc)::value;
+        rho += f[q];
+        if constexpr (cx(q) != 0) jx += cx(q) * f[q];
+        if constexpr (cy(q) != 0) jy += cy(q) * f[q];
+        if constexpr (cz(q) != 0) jz += cz(q) * f[q];
+        if constexpr (q < Q7) {
+            Na += a[q];
+            Nb += b[q];
+        }
+    });
+    float val;
+    switch (which) {
+    case LBPM_FIELD_PHI: {
+        const float Nt = Na + Nb;
+        val = Nt > 0.0f ? (Na - Nb) / Nt : 0.0f;
+        break;
+    }
+    case LBPM_FIELD_PRESSURE: val = rho / 3.0f; break;
+    case LBPM_FIELD_UX: val = jx + 0.5f * d.fx; break;
+    case LBPM_FIELD_UY: val = jy + 0.5f * d.fy; break;
+    case LBPM_FIELD_UZ: val = jz + 0.5f * d.fz; break;
+    case LBPM_FIELD_NA: val = Na; break;
+    case LBPM_FIELD_NB: val = Nb; break;
+    default: val = rho; break;
+    }
+    const int pv = d.site_vox[n];
+    const long long X = pv % px, r = pv / px, Y = r % py, Z = r / py;
+    dense[(X - 1) + static_cast<long long>(nx) * ((Y - 1) + static_cast<long long>(ny) * (Z - 1))] = val;
+}
+
+template <int PAR, class S>
+__global__ void __launch_bounds__(kBlock) k_export(DomainView d, int which, float* out) {
+    const int n = blockIdx.x * kBlock + threadIdx.x;
+    if (n >= d.n_sites) return;
+    float f[Q19], a[Q7], b[Q7];
+    load_site<PAR, S>(d, n, f, a, b);
+    const size_t N = d.n_sites;
+    if (which == LBPM_DIST_F) {
+#pragma unroll
+        for (int q = 0; q < Q19; ++q) out[q * N + n] = f[q];
+    } else {
+#pragma unroll
+        for (int q = 0; q < Q7; ++q) out[q * N + n] = which == LBPM_DIST_A ? a[q] : b[q];
+    }
+}
+
+template <int PAR, class S>
+__global__ void __launch_bounds__(kBlock) k_import(DomainView d, int which, const float* in) {
+    const int n = blockIdx.x * kBlock + threadIdx.x;
+    if (n >= d.n_sites) return;
+    const int v = d.site_vox[n];
+    int nb[Q19];
+    if constexpr (PAR == 1) {
+        static_for<1, Q19>([&](auto qc) {
+            constexpr int q = decltype(qc)::value;
+            nb[q] = __ldg(d.vsite + v + d.off[q]);
+        });
+    }
+    const size_t N = d.n_sites;
+    static_for<0, Q19>([&](auto qc) {
+        constexpr int q = decltype(qc)::value;
+        const size_t i = read_slot<PAR, q>(d, n, nb);
+        if (which == LBPM_DIST_F) S::template st_f<q>(d.f, i, in[q * N + n]);
+        if constexpr (q < Q7) {
+            if (which == LBPM_DIST_A) S::template st_c<q>(d.a, i, in[q * N + n]);
+            if (which == LBPM_DIST_B) S::template st_c<q>(d.b, i, in[q * N + n]);
+        }
+    });
+}
+
+template <template <int, class> class K, class... Args>
+cudaError_t dispatch(const lbpm_ctx* c, int parity, unsigned grid, cudaStream_t s, Args... args) {
+    if (grid == 0) return cudaSuccess;
+    const bool h = c->params.precision == LBPM_FP16;
+    (void)h;
+    if (parity == 0) {
+        if (h) K<0, StoreF16>::launch(grid, s, args...);
+        else K<0, StoreF32>::launch(grid, s, args...);
+    } else {
+        if (h) K<1, StoreF16>::launch(grid, s, args...);
+        else K<1, StoreF32>::launch(grid, s, args...);
+    }
+    return cudaGetLastError();
+}
+
+template <int PAR, class S>
+struct MeasureK {
+    static void launch(unsigned g, cudaStream_t s, DomainView d, double* p) {
+        k_measure<PAR, S><<<g, kBlock, 0, s>>>(d, p);
+    }
+};
+template <int PAR, class S>
+struct FieldK {
+    static void launch(unsigned g, cudaStream_t s, DomainView d, int w, int nx, int ny, int px, int py,
+                       float* o) {
+        k_field<PAR, S><<<g, kBlock, 0, s>>>(d, w, nx, ny, px, py, o);
+    }
+};
+template <int PAR, class S>
+struct ExportK {
+    static void launch(unsigned g, cudaStream_t s, DomainView d, int w, float* o) {
+        k_export<PAR, S><<<g, kBlock, 0, s>>>(d, w, o);
+    }
+};
+template <int PAR, class S>
+struct ImportK {
+    static void launch(unsigned g, cudaStream_t s, DomainView d, int w, const float* i) {
+        k_import<PAR, S><<<g, kBlock, 0, s>>>(d, w, i);
+    }
+};
+
+}  // namespace
+
+// d_out receives NSUM doubles. Uses c->d_partials (allocated on demand).
+cudaError_t launch_measure(lbpm_ctx* c, int parity, double* d_out, cudaStream_t s) {
+    long long nb = (c->N + kBlock - 1) / kBlock;
+    if (nb > kMeasureBlocks) nb = kMeasureBlocks;
+    if (nb < 1) nb = 1;
+    if (c->n_partials < nb) {
+        dfree(c, c->d_partials);
+        c->d_partials = static_cast<double*>(dalloc(c, sizeof(double) * NSUM * kMeasureBlocks));
+        if (!c->d_partials) return cudaErrorMemoryAllocation;
+        c->n_partials = kMeasureBlocks;
+    }
+    cudaError_t e = dispatch<MeasureK>(c, parity, static_cast<unsigned>(nb), s, make_view(c), c->d_partials);
+    if (e != cudaSuccess) return e;
+    k_reduce_partials<<<1, 32, 0, s>>>(c->d_partials, static_cast<int>(nb), d_out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_field(const lbpm_ctx* c, int parity, int which, float* dense, cudaStream_t s) {
+    k_fill<<<blocks_for(c->V), kBlock, 0, s>>>(dense, c->V, std::numeric_limits<float>::quiet_NaN());
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return dispatch<FieldK>(c, parity, blocks_for(c->N), s, make_view(c), which, c->nx, c->ny, c->px,
+                            c->py, dense);
+}
+
+cudaError_t launch_export_dist(const lbpm_ctx* c, int parity, int which, float* out, cudaStream_t s) {
+    return dispatch<ExportK>(c, parity, blocks_for(c->N), s, make_view(c), which, out);
+}
+
+cudaError_t launch_import_dist(const lbpm_ctx* c, int parity, int which, const float* in, cudaStream_t s) {
+    return dispatch<ImportK>(c, parity, blocks_for(c->N), s, make_view(c), which, in);
+}
+
+}  // namespace lbm

@@ -1,0 +1,149 @@
+// Single-domain launchers of the timestep kernels (Sec. 3.1) and fluid
+// initialisation.
+#include "step_kernels.cuh"
+
+namespace lbm {
+
+namespace {
+
+constexpr int kBlock = 256;
+
+template <int PAR, class S>
+__global__ void __launch_bounds__(kBlock) k_phase(DomainView d) {
+    const int t = blockIdx.x * kBlock + threadIdx.x;
+    phase_thread<PAR, S>(d, t);
+}
+
+template <int PAR, class S>
+__global__ void __launch_bounds__(kBlock) k_collide(DomainView d) {
+    const int n = blockIdx.x * kBlock + threadIdx.x;
+    if (n < d.n_sites) collide_thread<PAR, S>(d, n);
+}
+
+template <int PAR, class S>
+__global__ void __launch_bounds__(kBlock) k_reservoir(DomainView d, const int* sites,
+                                                      const signed char* side, int n_slab,
+                                                      float rho_in, float rho_out) {
+    const int i = blockIdx.x * kBlock + threadIdx.x;
+    if (i < n_slab) reservoir_thread<PAR, S>(d, sites[i], side[i], rho_in, rho_out);
+}
+
+// Initial state consistent with phi0 (rho = 1, u = 0), written in the even
+// (natural) layout: Na = (1 + phi0)/2, Nb = (1 - phi0)/2.
+template <class S>
+__global__ void __launch_bounds__(kBlock) k_init(DomainView d, const float* phi0, int nx, int ny,
+                                                 int px, int pxpy) {
+    const int n = blockIdx.x * kBlock + threadIdx.x;
+    if (n >= d.n_sites) return;
+    const int v = d.site_vox[n];
+    const int z = v / pxpy - 1;
+    const int r = v - (z + 1) * pxpy;
+    const int y = r / px - 1;
+    const int x = r - (y + 1) * px - 1;
+    float p = phi0[static_cast<size_t>(x) + static_cast<size_t>(nx) * (y + static_cast<size_t>(ny) * z)];
+    p = fminf(1.0f, fmaxf(-1.0f, p));
+    const float na = 0.5f * (1.0f + p), nb = 0.5f * (1.0f - p);
+    const size_t N = d.n_sites;
+    static_for<0, Q19>([&](auto qc) {
+        constexpr int q = decltype(qc)::value;
+        S::template st_f<q>(d.f, q * N + n, t19(q));
+        if constexpr (q < Q7) {
+            S::template st_c<q>(d.a, q * N + n, w7(q) * na);
+            S::template st_c<q>(d.b, q * N + n, w7(q) * nb);
+        }
+    });
+}
+
+inline unsigned blocks_for(long long n) { return static_cast<unsigned>((n + kBlock - 1) / kBlock); }
+
+}  // namespace
+
+DomainView make_view(const lbpm_ctx* c) {
+    DomainView d{};
+    d.n_sites = static_cast<int>(c->N);
+    d.n_halo = static_cast<int>(c->H);
+    for (int q = 0; q < Q19; ++q)
+        d.off[q] = cx(q) + cy(q) * c->px + cz(q) * c->px * c->py;
+    d.site_vox = c->d_site_vox;
+    d.vsite = c->d_vsite;
+    d.phi = c->d_phi;
+    d.halo_dst = c->d_halo_dst;
+    d.halo_site = c->d_halo_site;
+    d.nsum = c->d_nsum;
+    d.f = c->d_f;
+    d.a = c->d_a;
+    d.b = c->d_b;
+    const lbpm_params& p = c->params;
+    d.tau_a = static_cast<float>(p.tau_a);
+    d.tau_b = static_cast<float>(p.tau_b);
+    d.alpha = static_cast<float>(p.alpha);
+    d.beta = static_cast<float>(p.beta);
+    d.fx = static_cast<float>(p.force[0]);
+    d.fy = static_cast<float>(p.force[1]);
+    d.fz = static_cast<float>(p.force[2]);
+    d.uniform_tau = p.tau_a == p.tau_b;
+    const float s_nu = 1.0f / static_cast<float>(p.tau_a);
+    d.s_nu = s_nu;
+    d.s_m = 8.0f * (2.0f - s_nu) / (8.0f - s_nu);
+    return d;
+}
+
+cudaError_t launch_init_fluids(const lbpm_ctx* c, const float* phi0, cudaStream_t s) {
+    DomainView d = make_view(c);
+    if (c->N == 0) return cudaSuccess;
+    if (c->params.precision == LBPM_FP16)
+        k_init<StoreF16><<<blocks_for(c->N), kBlock, 0, s>>>(d, phi0, c->nx, c->ny, c->px, c->px * c->py);
+    else
+        k_init<StoreF32><<<blocks_for(c->N), kBlock, 0, s>>>(d, phi0, c->nx, c->ny, c->px, c->px * c->py);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_phase(const lbpm_ctx* c, int parity, cudaStream_t s) {
+    DomainView d = make_view(c);
+    const unsigned g = blocks_for(c->N + c->H);
+    if (g == 0) return cudaSuccess;
+    const bool h = c->params.precision == LBPM_FP16;
+    if (parity == 0) {
+        if (h) k_phase<0, StoreF16><<<g, kBlock, 0, s>>>(d);
+        else k_phase<0, StoreF32><<<g, kBlock, 0, s>>>(d);
+    } else {
+        if (h) k_phase<1, StoreF16><<<g, kBlock, 0, s>>>(d);
+        else k_phase<1, StoreF32><<<g, kBlock, 0, s>>>(d);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_collide(const lbpm_ctx* c, int parity, cudaStream_t s) {
+    DomainView d = make_view(c);
+    const unsigned g = blocks_for(c->N);
+    if (g == 0) return cudaSuccess;
+    const bool h = c->params.precision == LBPM_FP16;
+    if (parity == 0) {
+        if (h) k_collide<0, StoreF16><<<g, kBlock, 0, s>>>(d);
+        else k_collide<0, StoreF32><<<g, kBlock, 0, s>>>(d);
+    } else {
+        if (h) k_collide<1, StoreF16><<<g, kBlock, 0, s>>>(d);
+        else k_collide<1, StoreF32><<<g, kBlock, 0, s>>>(d);
+    }
+    return cudaGetLastError();
+}
+
+// parity = parity of the step that will READ the reset values
+cudaError_t launch_reservoir(const lbpm_ctx* c, int parity, cudaStream_t s) {
+    if (c->n_slab == 0) return cudaSuccess;
+    DomainView d = make_view(c);
+    const unsigned g = blocks_for(c->n_slab);
+    const int ns = static_cast<int>(c->n_slab);
+    const float ri = static_cast<float>(c->params.rho_in), ro = static_cast<float>(c->params.rho_out);
+    const bool h = c->params.precision == LBPM_FP16;
+    if (parity == 0) {
+        if (h) k_reservoir<0, StoreF16><<<g, kBlock, 0, s>>>(d, c->d_slab_site, c->d_slab_side, ns, ri, ro);
+        else k_reservoir<0, StoreF32><<<g, kBlock, 0, s>>>(d, c->d_slab_site, c->d_slab_side, ns, ri, ro);
+    } else {
+        if (h) k_reservoir<1, StoreF16><<<g, kBlock, 0, s>>>(d, c->d_slab_site, c->d_slab_side, ns, ri, ro);
+        else k_reservoir<1, StoreF32><<<g, kBlock, 0, s>>>(d, c->d_slab_site, c->d_slab_side, ns, ri, ro);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace lbm

@@ -1,0 +1,327 @@
+// Device code of one color-gradient LBM timestep (Sec. 3.1), shared by the
+// single-domain launchers and the batched launcher.
+//
+// State layout (structure of arrays, population-major, in place):
+//   F[q*N + n], A[q*N + n], B[q*N + n]
+// AA streaming: at an even step site n reads its own slots F[q][n] and writes
+// the post-collision value of direction q to F[opp(q)][n]. At an odd step it
+// reads direction q from F[opp(q)][m] where m is the upstream neighbour
+// (x - xi_q) or, if that voxel is solid, from F[q][n] (bounce-back), and it
+// writes direction q to F[q][m'] with m' = x + xi_q, or to F[opp(q)][n] when
+// x + xi_q is solid (halfway bounce-back). Each site reads and writes the same
+// slots within a step, so one array suffices and no two sites collide.
+#pragma once
+
+#include "internal.h"
+#include "lattice.cuh"
+
+namespace lbm {
+
+// ---------------------------------------------------------------------------
+// storage of the distributions
+// ---------------------------------------------------------------------------
+
+// Plain fp32 storage.
+struct StoreF32 {
+    template <int Q>
+    static __device__ __forceinline__ float ld_f(const void* p, size_t i) {
+        return static_cast<const float*>(p)[i];
+    }
+    template <int Q>
+    static __device__ __forceinline__ void st_f(void* p, size_t i, float v) {
+        static_cast<float*>(p)[i] = v;
+    }
+    template <int Q>
+    static __device__ __forceinline__ float ld_c(const void* p, size_t i) {
+        return static_cast<const float*>(p)[i];
+    }
+    template <int Q>
+    static __device__ __forceinline__ void st_c(void* p, size_t i, float v) {
+        static_cast<float*>(p)[i] = v;
+    }
+};
+
+// fp16 storage: momentum populations as deviations from the rest state
+// (f_q - t_q, rho = 1), component populations as plain fp16 values (their
+// rest state depends on the local composition, and a plain fp16 keeps full
+// relative precision near zero in the pure phases). The arithmetic stays fp32.
+struct StoreF16 {
+    template <int Q>
+    static __device__ __forceinline__ float ld_f(const void* p, size_t i) {
+        return t19(Q) + __half2float(static_cast<const __half*>(p)[i]);
+    }
+    template <int Q>
+    static __device__ __forceinline__ void st_f(void* p, size_t i, float v) {
+        static_cast<__half*>(p)[i] = __float2half_rn(v - t19(Q));
+    }
+    template <int Q>
+    static __device__ __forceinline__ float ld_c(const void* p, size_t i) {
+        return __half2float(static_cast<const __half*>(p)[i]);
+    }
+    template <int Q>
+    static __device__ __forceinline__ void st_c(void* p, size_t i, float v) {
+        static_cast<__half*>(p)[i] = __float2half_rn(v);
+    }
+};
+
+// ---------------------------------------------------------------------------
+// AA read map: where the value of direction Q of site n lives at a step of
+// parity PAR (the same slot the step writes direction opp(Q) to).
+// ---------------------------------------------------------------------------
+template <int PAR, int Q>
+__device__ __forceinline__ size_t read_slot(const DomainView& d, int n, const int* nb) {
+    const size_t N = static_cast<size_t>(d.n_sites);
+    if constexpr (Q == 0 || PAR == 0) {
+        return static_cast<size_t>(Q) * N + n;
+    } else {
+        // upstream site x - xi_Q = x + xi_opp(Q), or -1 (bounce-back)
+        const int up = nb[opp(Q)];
+        return up >= 0 ? static_cast<size_t>(opp(Q)) * N + up : static_cast<size_t>(Q) * N + n;
+    }
+}
+
+template <int PAR, int Q>
+__device__ __forceinline__ size_t write_slot(const DomainView& d, int n, const int* nb) {
+    const size_t N = static_cast<size_t>(d.n_sites);
+    if constexpr (Q == 0) {
+        return static_cast<size_t>(n);
+    } else if constexpr (PAR == 0) {
+        return static_cast<size_t>(opp(Q)) * N + n;
+    } else {
+        // downstream site x + xi_Q, or -1 (halfway bounce-back)
+        const int down = nb[Q];
+        return down >= 0 ? static_cast<size_t>(Q) * N + down : static_cast<size_t>(opp(Q)) * N + n;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// phase pass: Na, Nb -> phi (dense grid) and N (per site)          Sec. 3.1
+// ---------------------------------------------------------------------------
+template <int PAR, class S>
+__device__ __forceinline__ void phase_site(const DomainView& d, int n, int& v, float& Na, float& Nb) {
+    v = d.site_vox[n];
+    int nb[7];
+    if constexpr (PAR == 1) {
+        static_for<1, 7>([&](auto qc) {
+            constexpr int q = decltype(qc)::value;
+            nb[q] = __ldg(d.vsite + v + d.off[q]);
+        });
+    }
+    Na = 0.0f;
+    Nb = 0.0f;
+    static_for<0, 7>([&](auto qc) {
+        constexpr int q = decltype(qc)::value;
+        const size_t i = read_slot<PAR, q>(d, n, nb);
+        Na += S::template ld_c<q>(d.a, i);
+        Nb += S::template ld_c<q>(d.b, i);
+    });
+}
+
+__device__ __forceinline__ float phase_of(float Na, float Nb) {
+    const float Nt = Na + Nb;
+    return Nt > 0.0f ? (Na - Nb) / Nt : 0.0f;
+}
+
+template <int PAR, class S>
+__device__ __forceinline__ void phase_thread(const DomainView& d, int t) {
+    if (t < d.n_sites) {
+        int v;
+        float Na, Nb;
+        phase_site<PAR, S>(d, t, v, Na, Nb);
+        d.phi[v] = phase_of(Na, Nb);
+        d.nsum[t] = Na + Nb;
+    } else if (t < d.n_sites + d.n_halo) {
+        // halo voxel of a periodic face: mirror the phase of its source site
+        const int e = t - d.n_sites;
+        int v;
+        float Na, Nb;
+        phase_site<PAR, S>(d, __ldg(d.halo_site + e), v, Na, Nb);
+        d.phi[__ldg(d.halo_dst + e)] = phase_of(Na, Nb);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// fused collide + stream                                            Sec. 3.1
+// ---------------------------------------------------------------------------
+template <int PAR, class S>
+__device__ __forceinline__ void collide_thread(const DomainView& d, int n) {
+    const int v = __ldg(d.site_vox + n);
+
+    // neighbour sites for the odd-step gather / scatter
+    int nb[Q19];
+    if constexpr (PAR == 1) {
+        static_for<1, Q19>([&](auto qc) {
+            constexpr int q = decltype(qc)::value;
+            nb[q] = __ldg(d.vsite + v + d.off[q]);
+        });
+    }
+
+    // incoming distributions
+    float f[Q19];
+    static_for<0, Q19>([&](auto qc) {
+        constexpr int q = decltype(qc)::value;
+        f[q] = S::template ld_f<q>(d.f, read_slot<PAR, q>(d, n, nb));
+    });
+
+    // phase field: own value and the 18 neighbours (solids hold phi_s)
+    const float phi_c = __ldg(d.phi + v);
+    const float Nt = __ldg(d.nsum + n);
+    float p[Q19];
+    static_for<1, Q19>([&](auto qc) {
+        constexpr int q = decltype(qc)::value;
+        p[q] = __ldg(d.phi + v + d.off[q]);
+    });
+
+    // color gradient C = sum_q g_q xi_q phi(x + xi_q)
+    float Cx = 0.0f, Cy = 0.0f, Cz = 0.0f;
+    static_for<1, Q19>([&](auto qc) {
+        constexpr int q = decltype(qc)::value;
+        constexpr float g = grad_w(q);
+        if constexpr (cx(q) != 0) Cx = fmaf(g * cx(q), p[q], Cx);
+        if constexpr (cy(q) != 0) Cy = fmaf(g * cy(q), p[q], Cy);
+        if constexpr (cz(q) != 0) Cz = fmaf(g * cz(q), p[q], Cz);
+    });
+    const float Cmag = sqrtf(Cx * Cx + Cy * Cy + Cz * Cz);
+    float nx = 0.0f, ny = 0.0f, nz = 0.0f;
+    if (Cmag > 0.0f) {
+        const float inv = 1.0f / Cmag;
+        nx = Cx * inv;
+        ny = Cy * inv;
+        nz = Cz * inv;
+    }
+
+    // macroscopic moments
+    float rho = 0.0f, jx = 0.0f, jy = 0.0f, jz = 0.0f;
+    static_for<0, Q19>([&](auto qc) {
+        constexpr int q = decltype(qc)::value;
+        rho += f[q];
+        if constexpr (cx(q) > 0) jx += f[q];
+        if constexpr (cx(q) < 0) jx -= f[q];
+        if constexpr (cy(q) > 0) jy += f[q];
+        if constexpr (cy(q) < 0) jy -= f[q];
+        if constexpr (cz(q) > 0) jz += f[q];
+        if constexpr (cz(q) < 0) jz -= f[q];
+    });
+
+    // relaxation rates from the viscosity (tau mixed linearly in phi)
+    float s_nu = d.s_nu, s_m = d.s_m;
+    if (!d.uniform_tau) {
+        const float tau = d.tau_b + (d.tau_a - d.tau_b) * 0.5f * (1.0f + phi_c);
+        s_nu = 1.0f / tau;
+        s_m = 8.0f * (2.0f - s_nu) / (8.0f - s_nu);
+    }
+
+    // non-conserved moments (rows 1, 2 without their density part)
+    float m[Q19];
+    static_for<1, Q19>([&](auto kc) {
+        constexpr int k = decltype(kc)::value;
+        if constexpr (k != 3 && k != 5 && k != 7) {
+            float s = 0.0f;
+            static_for<0, Q19>([&](auto qc) {
+                constexpr int q = decltype(qc)::value;
+                constexpr int c = mrow_shifted(k, q);
+                if constexpr (c == 1) s += f[q];
+                else if constexpr (c == -1) s -= f[q];
+                else if constexpr (c != 0) s = fmaf(static_cast<float>(c), f[q], s);
+            });
+            m[k] = s;
+        }
+    });
+
+    // equilibria with the interfacial-tension terms (rho0 = 1)
+    const float jj = jx * jx + jy * jy + jz * jz;
+    const float ac = d.alpha * Cmag;
+    const float hac = 0.5f * ac;
+    float dm[Q19];
+    dm[1] = s_nu * ((19.0f * jj - ac) - m[1]);
+    dm[2] = s_nu * ((-5.5f * jj) - m[2]);
+    dm[4] = s_m * ((-2.0f / 3.0f) * jx - m[4]);
+    dm[6] = s_m * ((-2.0f / 3.0f) * jy - m[6]);
+    dm[8] = s_m * ((-2.0f / 3.0f) * jz - m[8]);
+    const float pxx = 2.0f * jx * jx - jy * jy - jz * jz;
+    const float pww = jy * jy - jz * jz;
+    dm[9] = s_nu * ((pxx + hac * (2.0f * nx * nx - ny * ny - nz * nz)) - m[9]);
+    dm[10] = s_nu * ((-0.5f * pxx) - m[10]);
+    dm[11] = s_nu * ((pww + hac * (ny * ny - nz * nz)) - m[11]);
+    dm[12] = s_nu * ((-0.5f * pww) - m[12]);
+    dm[13] = s_nu * ((jx * jy + hac * nx * ny) - m[13]);
+    dm[14] = s_nu * ((jy * jz + hac * ny * nz) - m[14]);
+    dm[15] = s_nu * ((jx * jz + hac * nx * nz) - m[15]);
+    dm[16] = -s_m * m[16];
+    dm[17] = -s_m * m[17];
+    dm[18] = -s_m * m[18];
+
+    // recoloring inputs: Na = N (1 + phi)/2, Nb = N (1 - phi)/2, so the
+    // weights Nb/N and Na/N are (1 - phi)/2 and (1 + phi)/2
+    const float Na = 0.5f * Nt * (1.0f + phi_c);
+    const float Nb = 0.5f * Nt * (1.0f - phi_c);
+    const float bxa = d.beta * 0.5f * (1.0f - phi_c);
+    const float bxb = d.beta * 0.5f * (1.0f + phi_c);
+
+    // post-collision f: f + M^-1 dm + 3 t_q xi_q . F, streamed on the fly
+    static_for<0, Q19>([&](auto qc) {
+        constexpr int q = decltype(qc)::value;
+        float acc = f[q];
+        static_for<1, Q19>([&](auto kc) {
+            constexpr int k = decltype(kc)::value;
+            if constexpr (k != 3 && k != 5 && k != 7) {
+                constexpr float c = minv(q, k);
+                if constexpr (mrow(k, q) != 0) acc = fmaf(c, dm[k], acc);
+            }
+        });
+        if constexpr (q > 0) {
+            constexpr float tw = 3.0f * t19(q);
+            float xf = 0.0f;
+            if constexpr (cx(q) != 0) xf += cx(q) * d.fx;
+            if constexpr (cy(q) != 0) xf += cy(q) * d.fy;
+            if constexpr (cz(q) != 0) xf += cz(q) * d.fz;
+            acc = fmaf(tw, xf, acc);
+        }
+        S::template st_f<q>(d.f, write_slot<PAR, q>(d, n, nb), acc);
+    });
+
+    // recolored component distributions (Eqs. LBE-mass-a/b), streamed on the fly
+    static_for<0, Q7>([&](auto qc) {
+        constexpr int q = decltype(qc)::value;
+        float ux = 0.0f, nn = 0.0f;
+        if constexpr (cx(q) != 0) { ux = cx(q) * jx; nn = cx(q) * nx; }
+        if constexpr (cy(q) != 0) { ux = cy(q) * jy; nn = cy(q) * ny; }
+        if constexpr (cz(q) != 0) { ux = cz(q) * jz; nn = cz(q) * nz; }
+        const float base = 1.0f + 4.5f * ux;
+        const float av = w7(q) * Na * (base + bxa * nn);
+        const float bv = w7(q) * Nb * (base - bxb * nn);
+        const size_t i = write_slot<PAR, q>(d, n, nb);
+        S::template st_c<q>(d.a, i, av);
+        S::template st_c<q>(d.b, i, bv);
+    });
+}
+
+// ---------------------------------------------------------------------------
+// reservoir reset (unsteady protocol, Sec. 4.1): write the rest state into
+// the slots the NEXT step (parity PAR) reads.
+// ---------------------------------------------------------------------------
+template <int PAR, class S>
+__device__ __forceinline__ void reservoir_thread(const DomainView& d, int n, int side, float rho_in,
+                                                 float rho_out) {
+    const int v = d.site_vox[n];
+    int nb[Q19];
+    if constexpr (PAR == 1) {
+        static_for<1, Q19>([&](auto qc) {
+            constexpr int q = decltype(qc)::value;
+            nb[q] = __ldg(d.vsite + v + d.off[q]);
+        });
+    }
+    const float rho = side == 1 ? rho_in : rho_out;
+    const float na = side == 1 ? 1.0f : 0.0f;
+    static_for<0, Q19>([&](auto qc) {
+        constexpr int q = decltype(qc)::value;
+        const size_t i = read_slot<PAR, q>(d, n, nb);
+        S::template st_f<q>(d.f, i, t19(q) * rho);
+        if constexpr (q < Q7) {
+            S::template st_c<q>(d.a, i, w7(q) * na);
+            S::template st_c<q>(d.b, i, w7(q) * (1.0f - na));
+        }
+    });
+}
+
+}  // namespace lbm
