@@ -48,7 +48,7 @@ typedef enum {
     LBPM_E_OOM = 2,       /* device allocation failed */
     LBPM_E_CUDA = 3,      /* a CUDA runtime call or kernel launch failed */
     LBPM_E_STATE = 4,     /* call out of order (e.g. advance before init) */
-    LBPM_E_UNSTABLE = 5,  /* the last measure found non-finite or negative densities */
+    LBPM_E_UNSTABLE = 5,  /* the last measure found non-finite values or a blown-up density */
     LBPM_E_TIMEOUT = 6    /* a bounded device-side wait gave up */
 } lbpm_status;
 
@@ -105,7 +105,8 @@ typedef struct {
  *                (eps_a mu_a |<u>_a| + eps_b mu_b |<u>_b|)/sigma with
  *                <u>_alpha = P_alpha/M_alpha, eps_alpha = vol_alpha/V,
  *                mu = (tau - 1/2)/3, sigma = 6 alpha
- *   status     = 0 ok, bit 0 non-finite value, bit 1 negative component density
+ *   status     = 0 ok, bit 0 a non-finite value, bit 1 a component density
+ *                below -1e-2 or a non-positive total density (instability)
  */
 typedef struct {
     long long step;

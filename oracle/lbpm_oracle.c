@@ -579,7 +579,10 @@ void orc_fields(const orc_t* o, double* phi, double* p, double* u) {
  *  0 step, 1 sat_mass, 2 sat_count, 3 mass_a, 4 mass_b, 5 mass_total (sum rho),
  *  6-8 mom_a, 9-11 mom_b, 12-14 flux, 15-17 flux_a, 18-20 flux_b,
  *  21 ke_a, 22 ke_b, 23 p_a, 24 p_b, 25 vol_a, 26 vol_b, 27 Ca, 28 n_sites,
- *  29 status (0 ok, 1 non-finite value, 2 negative component density). */
+ *  29 status (0 ok, bit 0 a non-finite value, bit 1 a component density below
+ *  -1e-2 or a non-positive total density). Small negative component densities
+ *  (order 1e-5) occur in valid runs next to interfaces, where a recolored
+ *  population can be negative, so they are not flagged. */
 void orc_measure(const orc_t* o, double* out) {
     for (int i = 0; i < NMEAS; ++i) out[i] = 0.0;
     const long long N = o->N;
@@ -601,8 +604,8 @@ void orc_measure(const orc_t* o, double* out) {
             for (int a = 0; a < 3; ++a) j[a] += XI[k][a] * fv;
         }
         if (!isfinite(Na) || !isfinite(Nb)) status |= 1;
-        if (Na < -1e-6 || Nb < -1e-6) status |= 2;
         const double Nt = Na + Nb;
+        if (Na < -1e-2 || Nb < -1e-2 || Nt <= 0.0 || rho <= 0.0) status |= 2;
         const double phi = Nt > 0.0 ? (Na - Nb) / Nt : 0.0;
         double u[3];
         for (int a = 0; a < 3; ++a) u[a] = (j[a] + 0.5 * o->F[a]) / RHO0;

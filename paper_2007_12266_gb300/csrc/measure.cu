@@ -52,7 +52,9 @@ __device__ __forceinline__ double warp_sum(double v) {
 // Sum layout (NSUM = 27):
 //  0 Na, 1 Nb, 2 rho, 3 #(phi > 0), 4-6 u, 7-9 (Na/N) u, 10-12 (Nb/N) u,
 //  13 M_a, 14 M_b, 15-17 P_a, 18-20 P_b, 21 K_a, 22 K_b, 23 p over A,
-//  24 p over B, 25 #non-finite, 26 #negative component density
+//  24 p over B, 25 #non-finite, 26 #sites with a component density below -1e-2
+//  or a non-positive total density (small negative densities are legitimate
+//  next to interfaces and are not counted)
 template <int PAR, class S>
 __global__ void __launch_bounds__(kBlock) k_measure(DomainView d, double* partials) {
     double acc[NSUM];
@@ -113,7 +115,7 @@ __global__ void __launch_bounds__(kBlock) k_measure(DomainView d, double* partia
             acc[24] += p;
         }
         if (!finite) acc[25] += 1.0;
-        if (Na < -1e-6 || Nb < -1e-6) acc[26] += 1.0;
+        if (Na < -1e-2 || Nb < -1e-2 || Nt <= 0.0 || rho <= 0.0) acc[26] += 1.0;
     }
     __shared__ double red[kBlock / 32][NSUM];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;

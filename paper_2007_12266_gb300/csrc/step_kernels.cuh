@@ -258,30 +258,38 @@ __device__ __forceinline__ void collide_thread(const DomainView& d, int n) {
     const float bxa = d.beta * 0.5f * (1.0f - phi_c);
     const float bxb = d.beta * 0.5f * (1.0f + phi_c);
 
-    // post-collision f: f + M^-1 dm + 3 t_q xi_q . F, streamed on the fly
-    static_for<0, Q19>([&](auto qc) {
+    // post-collision f: f + M^-1 dm + 3 t_q xi_q . F, streamed on the fly. The
+    // increments of the moving populations sum to minus the rest increment in
+    // exact arithmetic (columns of M^-1 are orthogonal to the density row and
+    // the force terms cancel in pairs); taking the rest increment as that sum
+    // keeps fp32 mass exact up to unbiased rounding.
+    float dsum = 0.0f;
+    static_for<1, Q19>([&](auto qc) {
         constexpr int q = decltype(qc)::value;
-        float acc = f[q];
+        float inc = 0.0f;
         static_for<1, Q19>([&](auto kc) {
             constexpr int k = decltype(kc)::value;
             if constexpr (k != 3 && k != 5 && k != 7) {
                 constexpr float c = minv(q, k);
-                if constexpr (mrow(k, q) != 0) acc = fmaf(c, dm[k], acc);
+                if constexpr (mrow(k, q) != 0) inc = fmaf(c, dm[k], inc);
             }
         });
-        if constexpr (q > 0) {
-            constexpr float tw = 3.0f * t19(q);
-            float xf = 0.0f;
-            if constexpr (cx(q) != 0) xf += cx(q) * d.fx;
-            if constexpr (cy(q) != 0) xf += cy(q) * d.fy;
-            if constexpr (cz(q) != 0) xf += cz(q) * d.fz;
-            acc = fmaf(tw, xf, acc);
-        }
-        S::template st_f<q>(d.f, write_slot<PAR, q>(d, n, nb), acc);
+        constexpr float tw = 3.0f * t19(q);
+        float xf = 0.0f;
+        if constexpr (cx(q) != 0) xf += cx(q) * d.fx;
+        if constexpr (cy(q) != 0) xf += cy(q) * d.fy;
+        if constexpr (cz(q) != 0) xf += cz(q) * d.fz;
+        inc = fmaf(tw, xf, inc);
+        dsum += inc;
+        S::template st_f<q>(d.f, write_slot<PAR, q>(d, n, nb), f[q] + inc);
     });
+    S::template st_f<0>(d.f, write_slot<PAR, 0>(d, n, nb), f[0] - dsum);
 
-    // recolored component distributions (Eqs. LBE-mass-a/b), streamed on the fly
-    static_for<0, Q7>([&](auto qc) {
+    // recolored component distributions (Eqs. LBE-mass-a/b), streamed on the
+    // fly; the rest populations take the remainder of Na and Nb so that the
+    // fp32 weights (whose sum is not exactly 1) create no mass
+    float asum = 0.0f, bsum = 0.0f;
+    static_for<1, Q7>([&](auto qc) {
         constexpr int q = decltype(qc)::value;
         float ux = 0.0f, nn = 0.0f;
         if constexpr (cx(q) != 0) { ux = cx(q) * jx; nn = cx(q) * nx; }
@@ -290,10 +298,15 @@ __device__ __forceinline__ void collide_thread(const DomainView& d, int n) {
         const float base = 1.0f + 4.5f * ux;
         const float av = w7(q) * Na * (base + bxa * nn);
         const float bv = w7(q) * Nb * (base - bxb * nn);
+        asum += av;
+        bsum += bv;
         const size_t i = write_slot<PAR, q>(d, n, nb);
         S::template st_c<q>(d.a, i, av);
         S::template st_c<q>(d.b, i, bv);
     });
+    const size_t i0 = write_slot<PAR, 0>(d, n, nb);
+    S::template st_c<0>(d.a, i0, Na - asum);
+    S::template st_c<0>(d.b, i0, Nb - bsum);
 }
 
 // ---------------------------------------------------------------------------

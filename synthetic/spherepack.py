@@ -126,7 +126,7 @@ def _gauss_smooth_periodic(x: np.ndarray, sigma: float) -> np.ndarray:
         s = [1] * len(shape)
         s[ax] = kk.size
         g = g * np.exp(-2.0 * (np.pi * sigma * kk.reshape(s)) ** 2)
-    return np.fft.irfftn(out * g, s=shape)
+    return np.fft.irfftn(out * g, s=shape, axes=tuple(range(len(shape))))
 
 
 def phi0_blob(labels: np.ndarray, sw: float, seed: int, sigma: float = 3.0) -> np.ndarray:

@@ -166,8 +166,8 @@ def test_read_fields_match_oracle():
     sv, _ = ref.index()
     pore = np.zeros(w.labels.size, bool)
     pore[sv] = True
-    for name, val, tol in (("phi", phi, 2e-6), ("pressure", p, 1e-7), ("ux", u[0], 1e-7),
-                           ("uy", u[1], 1e-7), ("uz", u[2], 1e-7)):
+    for name, val, tol in (("phi", phi, 2e-6), ("pressure", p, 1e-6 * p.max()), ("ux", u[0], 2e-7),
+                           ("uy", u[1], 2e-7), ("uz", u[2], 2e-7)):
         g = dom.read_field(name).ravel()
         assert np.isnan(g[~pore]).all()
         assert np.abs(g[sv] - val).max() <= tol, name
@@ -181,7 +181,7 @@ def test_mass_conservation_fp32():
     dom.advance(1000)
     m1 = dom.measure()
     for k in ("mass_a", "mass_b", "mass_total"):
-        assert abs(m1[k] / m0[k] - 1) < 1e-5, k
+        assert abs(m1[k] / m0[k] - 1) < 2e-6, k
 
 
 def test_reservoir_slabs_parity():
