@@ -54,7 +54,10 @@ lbpm_status enter(lbpm_ctx* c) {
     return LBPM_OK;
 }
 
+void drop_graphs(lbpm_ctx* c);
+
 void free_state(lbpm_ctx* c) {
+    drop_graphs(c);
     dfree(c, c->d_f);
     dfree(c, c->d_a);
     dfree(c, c->d_b);
@@ -102,6 +105,7 @@ lbpm_status alloc_state(lbpm_ctx* c) {
 
 // halo list (periodic mirrors of pore voxels) and reservoir site list
 lbpm_status build_boundaries(lbpm_ctx* c) {
+    drop_graphs(c);
     dfree(c, c->d_halo_dst);
     dfree(c, c->d_halo_site);
     c->d_halo_dst = c->d_halo_site = nullptr;
@@ -186,6 +190,41 @@ lbpm_status check_params(lbpm_ctx* c, const lbpm_params* p) {
     if (p->reservoir_z && p->periodic[2]) return fail(c, LBPM_E_INVALID, "reservoirs need a non-periodic z axis");
     if (!(p->rho_in > 0.0) || !(p->rho_out > 0.0)) return fail(c, LBPM_E_INVALID, "rho_in and rho_out must be > 0");
     return LBPM_OK;
+}
+
+void drop_graphs(lbpm_ctx* c) {
+    for (auto& g : c->graphs) {
+        if (g) cudaGraphExecDestroy(g);
+        g = nullptr;
+    }
+}
+
+// One timestep: phase pass, fused collide-stream, reservoir reset.
+cudaError_t enqueue_step(lbpm_ctx* c, int par, cudaStream_t s) {
+    cudaError_t e = launch_phase(c, par, s);
+    if (e == cudaSuccess) e = launch_collide(c, par, s);
+    if (e == cudaSuccess && c->n_slab) e = launch_reservoir(c, par ^ 1, s);
+    return e;
+}
+
+int kernels_per_step(const lbpm_ctx* c) { return c->n_slab ? 3 : 2; }
+
+// Capture `steps` (even) timesteps starting at an even step into a graph.
+cudaError_t capture_bundle(lbpm_ctx* c, int steps, cudaGraphExec_t* out) {
+    if (!c->cap_stream) {
+        cudaError_t e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return e;
+    }
+    cudaError_t e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return e;
+    cudaError_t el = cudaSuccess;
+    for (int k = 0; k < steps && el == cudaSuccess; ++k) el = enqueue_step(c, k & 1, c->cap_stream);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(c->cap_stream, &g);
+    if (el != cudaSuccess) e = el;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(out, g, 0);
+    if (g) cudaGraphDestroy(g);
+    return e;
 }
 
 int next_event(lbpm_ctx* c) {
@@ -275,6 +314,8 @@ lbpm_status lbpm_destroy(lbpm_ctx* c) {
     cudaSetDevice(c->device);
     if (c->stream) cudaStreamSynchronize(c->stream);
     else cudaDeviceSynchronize();
+    drop_graphs(c);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     while (!c->allocs.empty()) dfree(c, c->allocs.back().ptr);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
     delete c;
@@ -299,6 +340,7 @@ lbpm_status lbpm_set_params(lbpm_ctx* c, const lbpm_params* p) {
     if ((s = check_params(c, p))) return s;
     const lbpm_params old = c->params;
     c->params = *p;
+    drop_graphs(c);
     if (!c->have_image) return LBPM_OK;
     const bool per_changed = std::memcmp(old.periodic, p->periodic, sizeof old.periodic) != 0;
     if (per_changed || old.reservoir_z != p->reservoir_z) {
@@ -438,7 +480,27 @@ lbpm_status lbpm_advance(lbpm_ctx* c, long long nsteps) {
     if (nsteps < 0) return fail(c, LBPM_E_INVALID, "nsteps must be >= 0");
     if (!c->have_fluids) return fail(c, LBPM_E_STATE, "initialise the fluids first");
     if (c->unstable) return fail(c, LBPM_E_UNSTABLE, "the state was flagged unstable; re-initialise or restore");
-    for (long long k = 0; k < nsteps; ++k) {
+    long long k = 0;
+    if (!c->timing && c->use_graphs) {
+        // an odd start takes one plain step, then whole bundles run as graphs
+        if ((c->step & 1) && nsteps > 0) {
+            LBPM_CK(c, enqueue_step(c, 1, c->stream));
+            c->launches += kernels_per_step(c);
+            c->step += 1;
+            k = 1;
+        }
+        const int sizes[2] = {2, 16};
+        for (int gi = 1; gi >= 0; --gi) {
+            while (nsteps - k >= sizes[gi]) {
+                if (!c->graphs[gi]) LBPM_CK(c, capture_bundle(c, sizes[gi], &c->graphs[gi]));
+                LBPM_CK(c, cudaGraphLaunch(c->graphs[gi], c->stream));
+                c->launches += static_cast<long long>(sizes[gi]) * kernels_per_step(c);
+                c->step += sizes[gi];
+                k += sizes[gi];
+            }
+        }
+    }
+    for (; k < nsteps; ++k) {
         const int par = static_cast<int>(c->step & 1);
         int e0 = -1, e1 = -1, e2 = -1, e3 = -1;
         if (c->timing) {

@@ -77,6 +77,10 @@ struct lbpm_ctx {
     long long step = 0;
     long long launches = 0;
     int block = 256;
+    // captured step bundles: graphs[0] = 2 timesteps, graphs[1] = 16 timesteps
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t graphs[2] = {nullptr, nullptr};
+    bool use_graphs = true;
     // kernel timing
     bool timing = false;
     std::vector<cudaEvent_t> ev_pool;

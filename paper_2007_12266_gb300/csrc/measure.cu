@@ -64,28 +64,28 @@ __global__ void __launch_bounds__(kBlock) k_measure(DomainView d, double* partia
     for (int n = blockIdx.x * kBlock + threadIdx.x; n < d.n_sites; n += gridDim.x * kBlock) {
         float f[Q19], a[Q7], b[Q7];
         load_site<PAR, S>(d, n, f, a, b);
-        double Na = 0.0, Nb = 0.0, rho = 0.0, jx = 0.0, jy = 0.0, jz = 0.0;
+        // per-site quantities in fp32, accumulated in fp64
+        float Na = 0.0f, Nb = 0.0f, rho = 0.0f, jx = 0.0f, jy = 0.0f, jz = 0.0f;
         bool finite = true;
         static_for<0, Q19>([&](auto qc) {
             constexpr int q = decltype(qc)::value;
-            const double v = f[q];
             finite = finite && isfinite(f[q]);
-            rho += v;
-            if constexpr (cx(q) != 0) jx += cx(q) * v;
-            if constexpr (cy(q) != 0) jy += cy(q) * v;
-            if constexpr (cz(q) != 0) jz += cz(q) * v;
+            rho += f[q];
+            if constexpr (cx(q) != 0) jx += cx(q) * f[q];
+            if constexpr (cy(q) != 0) jy += cy(q) * f[q];
+            if constexpr (cz(q) != 0) jz += cz(q) * f[q];
             if constexpr (q < Q7) {
                 Na += a[q];
                 Nb += b[q];
             }
         });
         finite = finite && isfinite(Na) && isfinite(Nb);
-        const double Nt = Na + Nb;
-        const double phi = Nt > 0.0 ? (Na - Nb) / Nt : 0.0;
-        const double ux = jx + hfx, uy = jy + hfy, uz = jz + hfz;
-        const double uu = ux * ux + uy * uy + uz * uz;
-        const double p = rho / 3.0;
-        const double xa = Nt > 0.0 ? Na / Nt : 0.0, xb = Nt > 0.0 ? Nb / Nt : 0.0;
+        const float Nt = Na + Nb;
+        const float phi = Nt > 0.0f ? (Na - Nb) / Nt : 0.0f;
+        const float ux = jx + hfx, uy = jy + hfy, uz = jz + hfz;
+        const float uu = ux * ux + uy * uy + uz * uz;
+        const float p = rho * (1.0f / 3.0f);
+        const float xa = Nt > 0.0f ? Na / Nt : 0.0f, xb = Nt > 0.0f ? Nb / Nt : 0.0f;
         acc[0] += Na;
         acc[1] += Nb;
         acc[2] += rho;
@@ -98,7 +98,7 @@ __global__ void __launch_bounds__(kBlock) k_measure(DomainView d, double* partia
         acc[10] += xb * ux;
         acc[11] += xb * uy;
         acc[12] += xb * uz;
-        if (phi > 0.0) {
+        if (phi > 0.0f) {
             acc[3] += 1.0;
             acc[13] += rho;
             acc[15] += rho * ux;
@@ -115,7 +115,7 @@ __global__ void __launch_bounds__(kBlock) k_measure(DomainView d, double* partia
             acc[24] += p;
         }
         if (!finite) acc[25] += 1.0;
-        if (Na < -1e-2 || Nb < -1e-2 || Nt <= 0.0 || rho <= 0.0) acc[26] += 1.0;
+        if (Na < -1e-2f || Nb < -1e-2f || Nt <= 0.0f || rho <= 0.0f) acc[26] += 1.0;
     }
     __shared__ double red[kBlock / 32][NSUM];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -132,12 +132,15 @@ __global__ void __launch_bounds__(kBlock) k_measure(DomainView d, double* partia
     }
 }
 
+// one warp per quantity: lanes stride over the partials, then a shuffle tree
+// (fixed order, so the result is deterministic)
 __global__ void k_reduce_partials(const double* partials, int nblocks, double* out) {
-    const int i = threadIdx.x;
+    const int i = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (i >= NSUM) return;
     double s = 0.0;
-    for (int k = 0; k < nblocks; ++k) s += partials[static_cast<size_t>(k) * NSUM + i];
-    out[i] = s;
+    for (int k = lane; k < nblocks; k += 32) s += partials[static_cast<size_t>(k) * NSUM + i];
+    s = warp_sum(s);
+    if (lane == 0) out[i] = s;
 }
 
 __global__ void k_fill(float* p, long long n, float v) {
@@ -280,7 +283,7 @@ cudaError_t launch_measure(lbpm_ctx* c, int parity, double* d_out, cudaStream_t 
     }
     cudaError_t e = dispatch<MeasureK>(c, parity, static_cast<unsigned>(nb), s, make_view(c), c->d_partials);
     if (e != cudaSuccess) return e;
-    k_reduce_partials<<<1, 32, 0, s>>>(c->d_partials, static_cast<int>(nb), d_out);
+    k_reduce_partials<<<1, 32 * NSUM, 0, s>>>(c->d_partials, static_cast<int>(nb), d_out);
     return cudaGetLastError();
 }
 

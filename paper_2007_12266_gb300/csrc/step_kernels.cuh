@@ -21,8 +21,17 @@ namespace lbm {
 // storage of the distributions
 // ---------------------------------------------------------------------------
 
-// Plain fp32 storage.
+// Plain fp32 storage. ld_fdev / st_fdev exchange deviations f_q - t_q from
+// the rest state, which the collision works with.
 struct StoreF32 {
+    template <int Q>
+    static __device__ __forceinline__ float ld_fdev(const void* p, size_t i) {
+        return static_cast<const float*>(p)[i] - t19(Q);
+    }
+    template <int Q>
+    static __device__ __forceinline__ void st_fdev(void* p, size_t i, float dev) {
+        static_cast<float*>(p)[i] = t19(Q) + dev;
+    }
     template <int Q>
     static __device__ __forceinline__ float ld_f(const void* p, size_t i) {
         return static_cast<const float*>(p)[i];
@@ -47,6 +56,14 @@ struct StoreF32 {
 // relative precision near zero in the pure phases). The arithmetic stays fp32.
 struct StoreF16 {
     template <int Q>
+    static __device__ __forceinline__ float ld_fdev(const void* p, size_t i) {
+        return __half2float(static_cast<const __half*>(p)[i]);
+    }
+    template <int Q>
+    static __device__ __forceinline__ void st_fdev(void* p, size_t i, float dev) {
+        static_cast<__half*>(p)[i] = __float2half_rn(dev);
+    }
+    template <int Q>
     static __device__ __forceinline__ float ld_f(const void* p, size_t i) {
         return t19(Q) + __half2float(static_cast<const __half*>(p)[i]);
     }
@@ -63,6 +80,15 @@ struct StoreF16 {
         static_cast<__half*>(p)[i] = __float2half_rn(v);
     }
 };
+
+// Read-only load that the compiler may not merge with an earlier load of the
+// same address: re-reading a neighbour id from L1 is cheaper than keeping 18
+// of them live in registers across the collision.
+__device__ __forceinline__ int ld_fresh(const int* p) {
+    int v;
+    asm volatile("ld.global.nc.b32 %0, [%1];" : "=r"(v) : "l"(p));
+    return v;
+}
 
 // ---------------------------------------------------------------------------
 // AA read map: where the value of direction Q of site n lives at a step of
@@ -82,6 +108,7 @@ __device__ __forceinline__ size_t read_slot(const DomainView& d, int n, const in
 
 template <int PAR, int Q>
 __device__ __forceinline__ size_t write_slot(const DomainView& d, int n, const int* nb) {
+    (void)nb;
     const size_t N = static_cast<size_t>(d.n_sites);
     if constexpr (Q == 0) {
         return static_cast<size_t>(n);
@@ -90,6 +117,20 @@ __device__ __forceinline__ size_t write_slot(const DomainView& d, int n, const i
     } else {
         // downstream site x + xi_Q, or -1 (halfway bounce-back)
         const int down = nb[Q];
+        return down >= 0 ? static_cast<size_t>(Q) * N + down : static_cast<size_t>(opp(Q)) * N + n;
+    }
+}
+
+// write slot with the downstream neighbour re-read from the padded site grid
+template <int PAR, int Q>
+__device__ __forceinline__ size_t write_slot_v(const DomainView& d, int n, int v) {
+    const size_t N = static_cast<size_t>(d.n_sites);
+    if constexpr (Q == 0) {
+        return static_cast<size_t>(n);
+    } else if constexpr (PAR == 0) {
+        return static_cast<size_t>(opp(Q)) * N + n;
+    } else {
+        const int down = ld_fresh(d.vsite + v + d.off[Q]);
         return down >= 0 ? static_cast<size_t>(Q) * N + down : static_cast<size_t>(opp(Q)) * N + n;
     }
 }
@@ -156,11 +197,13 @@ __device__ __forceinline__ void collide_thread(const DomainView& d, int n) {
         });
     }
 
-    // incoming distributions
+    // incoming distributions, as deviations d_q = f_q - t_q from the rest
+    // state (exact in fp32 near rest), so that density and momentum are sums of
+    // small numbers and the relaxation acts on small quantities
     float f[Q19];
     static_for<0, Q19>([&](auto qc) {
         constexpr int q = decltype(qc)::value;
-        f[q] = S::template ld_f<q>(d.f, read_slot<PAR, q>(d, n, nb));
+        f[q] = S::template ld_fdev<q>(d.f, read_slot<PAR, q>(d, n, nb));
     });
 
     // phase field: own value and the 18 neighbours (solids hold phi_s)
@@ -190,11 +233,11 @@ __device__ __forceinline__ void collide_thread(const DomainView& d, int n) {
         nz = Cz * inv;
     }
 
-    // macroscopic moments
-    float rho = 0.0f, jx = 0.0f, jy = 0.0f, jz = 0.0f;
+    // macroscopic moments: drho = rho - 1 and j from the deviations
+    float drho = 0.0f, jx = 0.0f, jy = 0.0f, jz = 0.0f;
     static_for<0, Q19>([&](auto qc) {
         constexpr int q = decltype(qc)::value;
-        rho += f[q];
+        drho += f[q];
         if constexpr (cx(q) > 0) jx += f[q];
         if constexpr (cx(q) < 0) jx -= f[q];
         if constexpr (cy(q) > 0) jy += f[q];
@@ -211,45 +254,29 @@ __device__ __forceinline__ void collide_thread(const DomainView& d, int n) {
         s_m = 8.0f * (2.0f - s_nu) / (8.0f - s_nu);
     }
 
-    // non-conserved moments (rows 1, 2 without their density part)
-    float m[Q19];
-    static_for<1, Q19>([&](auto kc) {
-        constexpr int k = decltype(kc)::value;
-        if constexpr (k != 3 && k != 5 && k != 7) {
-            float s = 0.0f;
-            static_for<0, Q19>([&](auto qc) {
-                constexpr int q = decltype(qc)::value;
-                constexpr int c = mrow_shifted(k, q);
-                if constexpr (c == 1) s += f[q];
-                else if constexpr (c == -1) s -= f[q];
-                else if constexpr (c != 0) s = fmaf(static_cast<float>(c), f[q], s);
-            });
-            m[k] = s;
-        }
-    });
-
-    // equilibria with the interfacial-tension terms (rho0 = 1)
+    // MRT collision, evaluated in its equivalent two-relaxation-time form.
+    // With S from the viscosity, every non-conserved even moment (m1, m2,
+    // m9..m15) relaxes with s_nu and every non-conserved odd moment (m4, m6,
+    // m8, m16..m18) with s_m; the conserved ones equal their equilibria. So
+    //   f* = f - s_nu (f+ - feq+) - s_m (f- - feq-) + 3 t_q xi_q . F
+    // with f+- the even/odd parts over opposite pairs and feq the velocity-
+    // space equilibrium whose moments are m^eq:
+    //   feq+ = t_q (rho + 4.5 (xi.j)^2 - 1.5 j.j) + M^-1 dm_alpha
+    //   feq- = 3 t_q xi.j
+    // where dm_alpha holds the interfacial-tension terms of m1, m9, m11,
+    // m13, m14, m15 (rho0 = 1). Everything below is relative to the rest
+    // state t_q (rho = 1), i.e. in deviations.
     const float jj = jx * jx + jy * jy + jz * jz;
     const float ac = d.alpha * Cmag;
     const float hac = 0.5f * ac;
-    float dm[Q19];
-    dm[1] = s_nu * ((19.0f * jj - ac) - m[1]);
-    dm[2] = s_nu * ((-5.5f * jj) - m[2]);
-    dm[4] = s_m * ((-2.0f / 3.0f) * jx - m[4]);
-    dm[6] = s_m * ((-2.0f / 3.0f) * jy - m[6]);
-    dm[8] = s_m * ((-2.0f / 3.0f) * jz - m[8]);
-    const float pxx = 2.0f * jx * jx - jy * jy - jz * jz;
-    const float pww = jy * jy - jz * jz;
-    dm[9] = s_nu * ((pxx + hac * (2.0f * nx * nx - ny * ny - nz * nz)) - m[9]);
-    dm[10] = s_nu * ((-0.5f * pxx) - m[10]);
-    dm[11] = s_nu * ((pww + hac * (ny * ny - nz * nz)) - m[11]);
-    dm[12] = s_nu * ((-0.5f * pww) - m[12]);
-    dm[13] = s_nu * ((jx * jy + hac * nx * ny) - m[13]);
-    dm[14] = s_nu * ((jy * jz + hac * ny * nz) - m[14]);
-    dm[15] = s_nu * ((jx * jz + hac * nx * nz) - m[15]);
-    dm[16] = -s_m * m[16];
-    dm[17] = -s_m * m[17];
-    dm[18] = -s_m * m[18];
+    float dma[Q19];
+    dma[1] = -ac;
+    dma[9] = hac * (2.0f * nx * nx - ny * ny - nz * nz);
+    dma[11] = hac * (ny * ny - nz * nz);
+    dma[13] = hac * nx * ny;
+    dma[14] = hac * ny * nz;
+    dma[15] = hac * nx * nz;
+    const float drho_iso = drho - 1.5f * jj;
 
     // recoloring inputs: Na = N (1 + phi)/2, Nb = N (1 - phi)/2, so the
     // weights Nb/N and Na/N are (1 - phi)/2 and (1 + phi)/2
@@ -258,32 +285,36 @@ __device__ __forceinline__ void collide_thread(const DomainView& d, int n) {
     const float bxa = d.beta * 0.5f * (1.0f - phi_c);
     const float bxb = d.beta * 0.5f * (1.0f + phi_c);
 
-    // post-collision f: f + M^-1 dm + 3 t_q xi_q . F, streamed on the fly. The
-    // increments of the moving populations sum to minus the rest increment in
-    // exact arithmetic (columns of M^-1 are orthogonal to the density row and
-    // the force terms cancel in pairs); taking the rest increment as that sum
+    // The increments of the moving populations sum to minus the rest
+    // increment in exact arithmetic; taking the rest increment as that sum
     // keeps fp32 mass exact up to unbiased rounding.
     float dsum = 0.0f;
-    static_for<1, Q19>([&](auto qc) {
-        constexpr int q = decltype(qc)::value;
-        float inc = 0.0f;
-        static_for<1, Q19>([&](auto kc) {
+    static_for<0, 9>([&](auto pc) {
+        constexpr int q = 2 * decltype(pc)::value + 1;   // q odd, opp(q) = q + 1
+        constexpr int o = q + 1;
+        constexpr float t = t19(q);
+        float cu = 0.0f, xf = 0.0f;
+        if constexpr (cx(q) != 0) { cu += cx(q) * jx; xf += cx(q) * d.fx; }
+        if constexpr (cy(q) != 0) { cu += cy(q) * jy; xf += cy(q) * d.fy; }
+        if constexpr (cz(q) != 0) { cu += cz(q) * jz; xf += cz(q) * d.fz; }
+        float eqp = t * fmaf(4.5f * cu, cu, drho_iso);
+        static_for<1, 16>([&](auto kc) {
             constexpr int k = decltype(kc)::value;
-            if constexpr (k != 3 && k != 5 && k != 7) {
-                constexpr float c = minv(q, k);
-                if constexpr (mrow(k, q) != 0) inc = fmaf(c, dm[k], inc);
+            if constexpr (k == 1 || k == 9 || k == 11 || k == 13 || k == 14 || k == 15) {
+                if constexpr (mrow(k, q) != 0) eqp = fmaf(minv(q, k), dma[k], eqp);
             }
         });
-        constexpr float tw = 3.0f * t19(q);
-        float xf = 0.0f;
-        if constexpr (cx(q) != 0) xf += cx(q) * d.fx;
-        if constexpr (cy(q) != 0) xf += cy(q) * d.fy;
-        if constexpr (cz(q) != 0) xf += cz(q) * d.fz;
-        inc = fmaf(tw, xf, inc);
-        dsum += inc;
-        S::template st_f<q>(d.f, write_slot<PAR, q>(d, n, nb), f[q] + inc);
+        const float eqm = 3.0f * t * cu;
+        const float fp = 0.5f * (f[q] + f[o]);
+        const float fm = 0.5f * (f[q] - f[o]);
+        const float dp = -s_nu * (fp - eqp);
+        const float dmi = fmaf(3.0f * t, xf, -s_m * (fm - eqm));
+        const float inc_q = dp + dmi, inc_o = dp - dmi;
+        dsum += inc_q + inc_o;
+        S::template st_fdev<q>(d.f, write_slot_v<PAR, q>(d, n, v), f[q] + inc_q);
+        S::template st_fdev<o>(d.f, write_slot_v<PAR, o>(d, n, v), f[o] + inc_o);
     });
-    S::template st_f<0>(d.f, write_slot<PAR, 0>(d, n, nb), f[0] - dsum);
+    S::template st_fdev<0>(d.f, write_slot_v<PAR, 0>(d, n, v), f[0] - dsum);
 
     // recolored component distributions (Eqs. LBE-mass-a/b), streamed on the
     // fly; the rest populations take the remainder of Na and Nb so that the
@@ -300,11 +331,11 @@ __device__ __forceinline__ void collide_thread(const DomainView& d, int n) {
         const float bv = w7(q) * Nb * (base - bxb * nn);
         asum += av;
         bsum += bv;
-        const size_t i = write_slot<PAR, q>(d, n, nb);
+        const size_t i = write_slot_v<PAR, q>(d, n, v);
         S::template st_c<q>(d.a, i, av);
         S::template st_c<q>(d.b, i, bv);
     });
-    const size_t i0 = write_slot<PAR, 0>(d, n, nb);
+    const size_t i0 = write_slot_v<PAR, 0>(d, n, v);
     S::template st_c<0>(d.a, i0, Na - asum);
     S::template st_c<0>(d.b, i0, Nb - bsum);
 }

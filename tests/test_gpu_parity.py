@@ -301,3 +301,23 @@ def test_full_size_steady256_two_steps():
         ref.step(1)
         ef, ea, eb = compare_state(dom, ref)
         assert max(ef, ea, eb) <= 1e-6, (ef, ea, eb)
+
+
+def test_graph_bundles_match_plain_launches():
+    """advance() replays captured step bundles; with kernel timing on it
+    launches every kernel on its own. Both orders of work are the same, so the
+    states must be bit-identical, from an even and from an odd start."""
+    import paper_2007_12266_gb300 as lbm
+    w = workload_parity32()
+    doms = []
+    for timing in (False, True):
+        d = lbm.Domain(w.labels, w.affinity, periodic=w.periodic, **KW)
+        d.enable_kernel_timing(timing)
+        d.init_fluids(w.phi0)
+        d.advance(1)
+        d.advance(37)
+        d.advance(18)
+        doms.append(d)
+    for which in ("f", "a", "b"):
+        assert np.array_equal(doms[0].distributions(which), doms[1].distributions(which))
+    assert doms[0].step_count == doms[1].step_count == 56
