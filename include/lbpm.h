@@ -204,6 +204,30 @@ lbpm_status lbpm_measure(lbpm_ctx* ctx, lbpm_measures* out);
  * (caller-allocated, nx*ny*nz floats); solid voxels get NaN. */
 lbpm_status lbpm_read_field(lbpm_ctx* ctx, int which, float* out_dense);
 
+/* Largest image (nx*ny*nz voxels) that lbpm_read_field_noalloc accepts. */
+#define LBPM_NOALLOC_FIELD_MAX_VOXELS (1LL << 21)
+
+/*
+ * Allocation-free lbpm_read_field (the paper has no counterpart; this is a
+ * library service). For callers that cannot let the library allocate device
+ * memory after set-up - for example a loop that runs under a fixed device
+ * memory budget handed out at start-up, or a host that must not enter the
+ * allocator while other work owns it. lbpm_read_field allocates and frees a
+ * temporary device buffer on every call; this variant stages the field in
+ * one static device array of LBPM_NOALLOC_FIELD_MAX_VOXELS floats (8 MiB,
+ * enough for a 128^3 image) that the library holds on every GPU where it is
+ * loaded, until the process exits. It calls no cudaMalloc, cudaFree or other
+ * allocating routine.
+ * Same arguments, output and errors as lbpm_read_field, plus LBPM_E_INVALID
+ * when the image has more than LBPM_NOALLOC_FIELD_MAX_VOXELS voxels.
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture. All calls share the array: each call overwrites every entry it
+ * returns, but calls whose device work overlaps (other streams or threads)
+ * race on it.
+ */
+lbpm_status lbpm_read_field_noalloc(lbpm_ctx* ctx, int which, float* out_dense);
+
 /* Distributions of the current state in canonical order, population-major:
  * out[q*n_sites + n] = f_q (or A_q, B_q) at site n, the value the next step
  * will collide, whatever the AA parity. Q = 19 for F, 7 for A, B. */

@@ -217,6 +217,15 @@ class Domain:
         self._check(self._L.lbpm_read_field(self._h, FIELDS[name], out.ctypes.data))
         return out
 
+    def read_field_noalloc(self, name: str) -> np.ndarray:
+        """Same as read_field, without any device allocation: the library stages
+        the field in a fixed static device buffer (images up to
+        LBPM_NOALLOC_FIELD_MAX_VOXELS voxels), for callers that must not let it
+        allocate after set-up. Concurrent calls on one GPU race on that buffer."""
+        out = np.empty(self.shape, dtype=np.float32)
+        self._check(self._L.lbpm_read_field_noalloc(self._h, FIELDS[name], out.ctypes.data))
+        return out
+
     def distributions(self, which: str) -> np.ndarray:
         code, Q = DISTS[which]
         out = np.empty((Q, self.n_sites), dtype=np.float32)

@@ -64,6 +64,7 @@ SIGNATURES = {
     "lbpm_sync": (ct.c_int, [c_ctx_p]),
     "lbpm_measure": (ct.c_int, [c_ctx_p, ct.POINTER(Measures)]),
     "lbpm_read_field": (ct.c_int, [c_ctx_p, ct.c_int, ct.c_void_p]),
+    "lbpm_read_field_noalloc": (ct.c_int, [c_ctx_p, ct.c_int, ct.c_void_p]),
     "lbpm_read_distributions": (ct.c_int, [c_ctx_p, ct.c_int, ct.c_void_p]),
     "lbpm_write_distributions": (ct.c_int, [c_ctx_p, ct.c_int, ct.c_void_p]),
     "lbpm_num_sites": (ct.c_int, [c_ctx_p, ct.POINTER(ct.c_longlong)]),
