@@ -62,8 +62,11 @@ void free_state(lbpm_ctx* c) {
     dfree(c, c->d_a);
     dfree(c, c->d_b);
     dfree(c, c->d_nsum);
+    dfree(c, c->d_nab[0]);
+    dfree(c, c->d_nab[1]);
     c->d_f = c->d_a = c->d_b = nullptr;
     c->d_nsum = nullptr;
+    c->d_nab[0] = c->d_nab[1] = nullptr;
     c->have_fluids = false;
 }
 
@@ -95,8 +98,16 @@ lbpm_status alloc_state(lbpm_ctx* c) {
     c->d_f = dalloc(c, state_bytes(c, 19));
     c->d_a = dalloc(c, state_bytes(c, 7));
     c->d_b = dalloc(c, state_bytes(c, 7));
-    c->d_nsum = static_cast<float*>(dalloc(c, sizeof(float) * c->N));
-    if (!c->d_f || !c->d_a || !c->d_b || !c->d_nsum) {
+    bool ok = c->d_f && c->d_a && c->d_b;
+    if (c->params.precision == LBPM_FP16) {
+        c->d_nab[0] = static_cast<float2*>(dalloc(c, sizeof(float2) * c->N));
+        c->d_nab[1] = static_cast<float2*>(dalloc(c, sizeof(float2) * c->N));
+        ok = ok && c->d_nab[0] && c->d_nab[1];
+    } else {
+        c->d_nsum = static_cast<float*>(dalloc(c, sizeof(float) * c->N));
+        ok = ok && c->d_nsum;
+    }
+    if (!ok) {
         free_state(c);
         return fail(c, LBPM_E_OOM, "device allocation of the distributions failed");
     }

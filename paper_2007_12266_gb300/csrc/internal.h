@@ -25,7 +25,9 @@ struct DomainView {
     float* phi;            // [Vp] phase field; solids hold phi_s, walls 0
     const int* halo_dst;   // [H] padded halo voxel
     const int* halo_site;  // [H] site it mirrors
-    float* nsum;           // [N] Na + Nb of the current step (phase pass -> collision)
+    float* nsum;           // [N] Na + Nb of the current step (phase pass -> collision), fp32 store
+    float2* nab[2];        // [N] (Na, Nb) per site by step parity, fp16 store: the reference of the
+                           //     stored component deviations and the phase pass -> collision hand-off
     void* f;               // [19][N] momentum distributions (AA in place)
     void* a;               // [7][N]  component A
     void* b;               // [7][N]  component B
@@ -63,7 +65,8 @@ struct lbpm_ctx {
     float* d_phi = nullptr;         // [Vp]
     int* d_halo_dst = nullptr;      // [H]
     int* d_halo_site = nullptr;     // [H]
-    float* d_nsum = nullptr;        // [N]
+    float* d_nsum = nullptr;        // [N] fp32 store
+    float2* d_nab[2] = {nullptr, nullptr};  // [N] each, fp16 store
     void* d_f = nullptr;
     void* d_a = nullptr;
     void* d_b = nullptr;

@@ -26,7 +26,7 @@ __device__ __forceinline__ void load_site(const DomainView& d, int n, float (&f)
                                           float (&b)[Q7]) {
     const int v = d.site_vox[n];
     int nb[Q19];
-    if constexpr (PAR == 1) {
+    if constexpr (PAR == 1 || S::kRef) {
         static_for<1, Q19>([&](auto qc) {
             constexpr int q = decltype(qc)::value;
             nb[q] = __ldg(d.vsite + v + d.off[q]);
@@ -34,14 +34,25 @@ __device__ __forceinline__ void load_site(const DomainView& d, int n, float (&f)
     }
     static_for<0, Q19>([&](auto qc) {
         constexpr int q = decltype(qc)::value;
-        const size_t i = read_slot<PAR, q>(d, n, nb);
-        f[q] = S::template ld_f<q>(d.f, i);
-        if constexpr (q < Q7) {
-            a[q] = S::template ld_c<q>(d.a, i);
-            b[q] = S::template ld_c<q>(d.b, i);
-        }
+        f[q] = S::template ld_f<q>(d.f, read_slot<PAR, q>(d, n, nb));
     });
+    load_components<PAR, S>(d, n, nb, a, b);
 }
+
+// Compensated fp32 accumulator (TwoSum): hi + lo carries about 48 bits, so a
+// thread's few dozen sites sum as accurately as in fp64 while using the fp32
+// pipes; block and global reductions are fp64.
+struct Acc2 {
+    float hi = 0.0f, lo = 0.0f;
+    __device__ __forceinline__ void add(float x) {
+        const float s = hi + x;
+        const float bp = s - hi;
+        const float err = (hi - (s - bp)) + (x - bp);
+        hi = s;
+        lo += err;
+    }
+    __device__ __forceinline__ double value() const { return static_cast<double>(hi) + static_cast<double>(lo); }
+};
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -57,9 +68,7 @@ __device__ __forceinline__ double warp_sum(double v) {
 //  next to interfaces and are not counted)
 template <int PAR, class S>
 __global__ void __launch_bounds__(kBlock) k_measure(DomainView d, double* partials) {
-    double acc[NSUM];
-#pragma unroll
-    for (int i = 0; i < NSUM; ++i) acc[i] = 0.0;
+    Acc2 acc[NSUM];
     const float hfx = 0.5f * d.fx, hfy = 0.5f * d.fy, hfz = 0.5f * d.fz;
     for (int n = blockIdx.x * kBlock + threadIdx.x; n < d.n_sites; n += gridDim.x * kBlock) {
         float f[Q19], a[Q7], b[Q7];
@@ -86,42 +95,42 @@ __global__ void __launch_bounds__(kBlock) k_measure(DomainView d, double* partia
         const float uu = ux * ux + uy * uy + uz * uz;
         const float p = rho * (1.0f / 3.0f);
         const float xa = Nt > 0.0f ? Na / Nt : 0.0f, xb = Nt > 0.0f ? Nb / Nt : 0.0f;
-        acc[0] += Na;
-        acc[1] += Nb;
-        acc[2] += rho;
-        acc[4] += ux;
-        acc[5] += uy;
-        acc[6] += uz;
-        acc[7] += xa * ux;
-        acc[8] += xa * uy;
-        acc[9] += xa * uz;
-        acc[10] += xb * ux;
-        acc[11] += xb * uy;
-        acc[12] += xb * uz;
+        acc[0].add(Na);
+        acc[1].add(Nb);
+        acc[2].add(rho);
+        acc[4].add(ux);
+        acc[5].add(uy);
+        acc[6].add(uz);
+        acc[7].add(xa * ux);
+        acc[8].add(xa * uy);
+        acc[9].add(xa * uz);
+        acc[10].add(xb * ux);
+        acc[11].add(xb * uy);
+        acc[12].add(xb * uz);
         if (phi > 0.0f) {
-            acc[3] += 1.0;
-            acc[13] += rho;
-            acc[15] += rho * ux;
-            acc[16] += rho * uy;
-            acc[17] += rho * uz;
-            acc[21] += rho * uu;
-            acc[23] += p;
+            acc[3].add(1.0);
+            acc[13].add(rho);
+            acc[15].add(rho * ux);
+            acc[16].add(rho * uy);
+            acc[17].add(rho * uz);
+            acc[21].add(rho * uu);
+            acc[23].add(p);
         } else {
-            acc[14] += rho;
-            acc[18] += rho * ux;
-            acc[19] += rho * uy;
-            acc[20] += rho * uz;
-            acc[22] += rho * uu;
-            acc[24] += p;
+            acc[14].add(rho);
+            acc[18].add(rho * ux);
+            acc[19].add(rho * uy);
+            acc[20].add(rho * uz);
+            acc[22].add(rho * uu);
+            acc[24].add(p);
         }
-        if (!finite) acc[25] += 1.0;
-        if (Na < -1e-2f || Nb < -1e-2f || Nt <= 0.0f || rho <= 0.0f) acc[26] += 1.0;
+        if (!finite) acc[25].add(1.0);
+        if (Na < -1e-2f || Nb < -1e-2f || Nt <= 0.0f || rho <= 0.0f) acc[26].add(1.0);
     }
     __shared__ double red[kBlock / 32][NSUM];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
     for (int i = 0; i < NSUM; ++i) {
-        const double s = warp_sum(acc[i]);
+        const double s = warp_sum(acc[i].value());
         if (lane == 0) red[w][i] = s;
     }
     __syncthreads();
@@ -203,13 +212,29 @@ __global__ void __launch_bounds__(kBlock) k_export(DomainView d, int which, floa
     }
 }
 
+// fp16 store: the reference densities of imported component populations are
+// the sums of the imported values at each site (any reference works as long
+// as the reader uses the same one).
+template <int PAR>
+__global__ void __launch_bounds__(kBlock) k_import_ref(DomainView d, int which, const float* in) {
+    const int n = blockIdx.x * kBlock + threadIdx.x;
+    if (n >= d.n_sites) return;
+    const size_t N = d.n_sites;
+    float s = 0.0f;
+#pragma unroll
+    for (int q = 0; q < Q7; ++q) s += in[q * N + n];
+    float2* ref = d.nab[PAR ^ 1] + n;
+    if (which == LBPM_DIST_A) ref->x = s;
+    else ref->y = s;
+}
+
 template <int PAR, class S>
 __global__ void __launch_bounds__(kBlock) k_import(DomainView d, int which, const float* in) {
     const int n = blockIdx.x * kBlock + threadIdx.x;
     if (n >= d.n_sites) return;
     const int v = d.site_vox[n];
     int nb[Q19];
-    if constexpr (PAR == 1) {
+    if constexpr (PAR == 1 || S::kRef) {
         static_for<1, Q19>([&](auto qc) {
             constexpr int q = decltype(qc)::value;
             nb[q] = __ldg(d.vsite + v + d.off[q]);
@@ -221,8 +246,15 @@ __global__ void __launch_bounds__(kBlock) k_import(DomainView d, int which, cons
         const size_t i = read_slot<PAR, q>(d, n, nb);
         if (which == LBPM_DIST_F) S::template st_f<q>(d.f, i, in[q * N + n]);
         if constexpr (q < Q7) {
-            if (which == LBPM_DIST_A) S::template st_c<q>(d.a, i, in[q * N + n]);
-            if (which == LBPM_DIST_B) S::template st_c<q>(d.b, i, in[q * N + n]);
+            if (which != LBPM_DIST_F) {
+                float val = in[q * N + n];
+                if constexpr (S::kRef) {
+                    const float2 r = d.nab[PAR ^ 1][writer_of<q>(n, nb)];
+                    val -= w7(q) * (which == LBPM_DIST_A ? r.x : r.y);
+                }
+                if (which == LBPM_DIST_A) S::template st_c<q>(d.a, i, val);
+                else S::template st_c<q>(d.b, i, val);
+            }
         }
     });
 }
@@ -300,6 +332,12 @@ cudaError_t launch_export_dist(const lbpm_ctx* c, int parity, int which, float* 
 }
 
 cudaError_t launch_import_dist(const lbpm_ctx* c, int parity, int which, const float* in, cudaStream_t s) {
+    if (c->params.precision == LBPM_FP16 && which != LBPM_DIST_F && c->N > 0) {
+        if (parity == 0) k_import_ref<0><<<blocks_for(c->N), kBlock, 0, s>>>(make_view(c), which, in);
+        else k_import_ref<1><<<blocks_for(c->N), kBlock, 0, s>>>(make_view(c), which, in);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
     return dispatch<ImportK>(c, parity, blocks_for(c->N), s, make_view(c), which, in);
 }
 

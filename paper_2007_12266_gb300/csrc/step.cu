@@ -8,6 +8,22 @@ namespace {
 
 constexpr int kBlock = 256;
 
+// Launch with programmatic stream serialization (see wait_prior_grid()).
+template <class... KArgs, class... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), unsigned grid, cudaStream_t s, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(kBlock);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 template <int PAR, class S>
 __global__ void __launch_bounds__(kBlock) k_phase(DomainView d) {
     const int t = blockIdx.x * kBlock + threadIdx.x;
@@ -28,6 +44,27 @@ __global__ void __launch_bounds__(kBlock) k_reservoir(DomainView d, const int* s
     if (i < n_slab) reservoir_thread<PAR, S>(d, sites[i], side[i], rho_in, rho_out);
 }
 
+__device__ __forceinline__ float phi0_of_site(const DomainView& d, int n, const float* phi0, int nx, int ny,
+                                              int px, int pxpy) {
+    const int v = d.site_vox[n];
+    const int z = v / pxpy - 1;
+    const int r = v - (z + 1) * pxpy;
+    const int y = r / px - 1;
+    const int x = r - (y + 1) * px - 1;
+    const float p = phi0[static_cast<size_t>(x) + static_cast<size_t>(nx) * (y + static_cast<size_t>(ny) * z)];
+    return fminf(1.0f, fmaxf(-1.0f, p));
+}
+
+// fp16 store: densities of the initial state, as if written by a step -1 (the
+// reference of the component deviations read at step 0).
+__global__ void __launch_bounds__(kBlock) k_init_ref(DomainView d, const float* phi0, int nx, int ny, int px,
+                                                     int pxpy) {
+    const int n = blockIdx.x * kBlock + threadIdx.x;
+    if (n >= d.n_sites) return;
+    const float p = phi0_of_site(d, n, phi0, nx, ny, px, pxpy);
+    d.nab[1][n] = make_float2(0.5f * (1.0f + p), 0.5f * (1.0f - p));
+}
+
 // Initial state consistent with phi0 (rho = 1, u = 0), written in the even
 // (natural) layout: Na = (1 + phi0)/2, Nb = (1 - phi0)/2.
 template <class S>
@@ -35,21 +72,29 @@ __global__ void __launch_bounds__(kBlock) k_init(DomainView d, const float* phi0
                                                  int px, int pxpy) {
     const int n = blockIdx.x * kBlock + threadIdx.x;
     if (n >= d.n_sites) return;
-    const int v = d.site_vox[n];
-    const int z = v / pxpy - 1;
-    const int r = v - (z + 1) * pxpy;
-    const int y = r / px - 1;
-    const int x = r - (y + 1) * px - 1;
-    float p = phi0[static_cast<size_t>(x) + static_cast<size_t>(nx) * (y + static_cast<size_t>(ny) * z)];
-    p = fminf(1.0f, fmaxf(-1.0f, p));
+    const float p = phi0_of_site(d, n, phi0, nx, ny, px, pxpy);
     const float na = 0.5f * (1.0f + p), nb = 0.5f * (1.0f - p);
+    int nbr[Q7];
+    if constexpr (S::kRef) {
+        const int v = d.site_vox[n];
+        static_for<1, Q7>([&](auto qc) {
+            constexpr int q = decltype(qc)::value;
+            nbr[q] = __ldg(d.vsite + v + d.off[q]);
+        });
+    }
     const size_t N = d.n_sites;
     static_for<0, Q19>([&](auto qc) {
         constexpr int q = decltype(qc)::value;
         S::template st_f<q>(d.f, q * N + n, t19(q));
         if constexpr (q < Q7) {
-            S::template st_c<q>(d.a, q * N + n, w7(q) * na);
-            S::template st_c<q>(d.b, q * N + n, w7(q) * nb);
+            float av = w7(q) * na, bv = w7(q) * nb;
+            if constexpr (S::kRef) {
+                const float2 r = d.nab[1][writer_of<q>(n, nbr)];
+                av -= w7(q) * r.x;
+                bv -= w7(q) * r.y;
+            }
+            S::template st_c<q>(d.a, q * N + n, av);
+            S::template st_c<q>(d.b, q * N + n, bv);
         }
     });
 }
@@ -70,6 +115,8 @@ DomainView make_view(const lbpm_ctx* c) {
     d.halo_dst = c->d_halo_dst;
     d.halo_site = c->d_halo_site;
     d.nsum = c->d_nsum;
+    d.nab[0] = c->d_nab[0];
+    d.nab[1] = c->d_nab[1];
     d.f = c->d_f;
     d.a = c->d_a;
     d.b = c->d_b;
@@ -91,9 +138,10 @@ DomainView make_view(const lbpm_ctx* c) {
 cudaError_t launch_init_fluids(const lbpm_ctx* c, const float* phi0, cudaStream_t s) {
     DomainView d = make_view(c);
     if (c->N == 0) return cudaSuccess;
-    if (c->params.precision == LBPM_FP16)
+    if (c->params.precision == LBPM_FP16) {
+        k_init_ref<<<blocks_for(c->N), kBlock, 0, s>>>(d, phi0, c->nx, c->ny, c->px, c->px * c->py);
         k_init<StoreF16><<<blocks_for(c->N), kBlock, 0, s>>>(d, phi0, c->nx, c->ny, c->px, c->px * c->py);
-    else
+    } else
         k_init<StoreF32><<<blocks_for(c->N), kBlock, 0, s>>>(d, phi0, c->nx, c->ny, c->px, c->px * c->py);
     return cudaGetLastError();
 }
@@ -103,14 +151,8 @@ cudaError_t launch_phase(const lbpm_ctx* c, int parity, cudaStream_t s) {
     const unsigned g = blocks_for(c->N + c->H);
     if (g == 0) return cudaSuccess;
     const bool h = c->params.precision == LBPM_FP16;
-    if (parity == 0) {
-        if (h) k_phase<0, StoreF16><<<g, kBlock, 0, s>>>(d);
-        else k_phase<0, StoreF32><<<g, kBlock, 0, s>>>(d);
-    } else {
-        if (h) k_phase<1, StoreF16><<<g, kBlock, 0, s>>>(d);
-        else k_phase<1, StoreF32><<<g, kBlock, 0, s>>>(d);
-    }
-    return cudaGetLastError();
+    if (parity == 0) return h ? launch_pdl(k_phase<0, StoreF16>, g, s, d) : launch_pdl(k_phase<0, StoreF32>, g, s, d);
+    return h ? launch_pdl(k_phase<1, StoreF16>, g, s, d) : launch_pdl(k_phase<1, StoreF32>, g, s, d);
 }
 
 cudaError_t launch_collide(const lbpm_ctx* c, int parity, cudaStream_t s) {
@@ -118,14 +160,9 @@ cudaError_t launch_collide(const lbpm_ctx* c, int parity, cudaStream_t s) {
     const unsigned g = blocks_for(c->N);
     if (g == 0) return cudaSuccess;
     const bool h = c->params.precision == LBPM_FP16;
-    if (parity == 0) {
-        if (h) k_collide<0, StoreF16><<<g, kBlock, 0, s>>>(d);
-        else k_collide<0, StoreF32><<<g, kBlock, 0, s>>>(d);
-    } else {
-        if (h) k_collide<1, StoreF16><<<g, kBlock, 0, s>>>(d);
-        else k_collide<1, StoreF32><<<g, kBlock, 0, s>>>(d);
-    }
-    return cudaGetLastError();
+    if (parity == 0)
+        return h ? launch_pdl(k_collide<0, StoreF16>, g, s, d) : launch_pdl(k_collide<0, StoreF32>, g, s, d);
+    return h ? launch_pdl(k_collide<1, StoreF16>, g, s, d) : launch_pdl(k_collide<1, StoreF32>, g, s, d);
 }
 
 // parity = parity of the step that will READ the reset values

@@ -24,6 +24,7 @@ namespace lbm {
 // Plain fp32 storage. ld_fdev / st_fdev exchange deviations f_q - t_q from
 // the rest state, which the collision works with.
 struct StoreF32 {
+    static constexpr bool kRef = false;   // component values stored as they are
     template <int Q>
     static __device__ __forceinline__ float ld_fdev(const void* p, size_t i) {
         return static_cast<const float*>(p)[i] - t19(Q);
@@ -50,36 +51,53 @@ struct StoreF32 {
     }
 };
 
-// fp16 storage: momentum populations as deviations from the rest state
-// (f_q - t_q, rho = 1), component populations as plain fp16 values (their
-// rest state depends on the local composition, and a plain fp16 keeps full
-// relative precision near zero in the pure phases). The arithmetic stays fp32.
+// fp16 storage of deviations from the rest-state equilibrium, arithmetic in
+// fp32. Momentum populations: f_q - t_q (rest state rho = 1). Component
+// populations: A_q - w_q Na(s), B_q - w_q Nb(s), where s is the site that
+// wrote the value and Na(s), Nb(s) its densities at that step, kept in fp32
+// per site (DomainView::nab). Storing the values themselves lets every site of
+// a pure phase round the same value the same way on the fp16 grid, a biased
+// error that leaked 3e-3 of the component mass per 1,000 steps; the
+// deviations are small in the bulk, so their rounding is negligible there.
+// Values are scaled by 2^14 (an exact power of two) to keep small deviations
+// out of fp16's subnormal range; |deviation| up to 4 stays representable.
 struct StoreF16 {
+    static constexpr bool kRef = true;
+    static constexpr float kScale = 16384.0f;
+    static constexpr float kInv = 1.0f / 16384.0f;
     template <int Q>
     static __device__ __forceinline__ float ld_fdev(const void* p, size_t i) {
-        return __half2float(static_cast<const __half*>(p)[i]);
+        return __half2float(static_cast<const __half*>(p)[i]) * kInv;
     }
     template <int Q>
     static __device__ __forceinline__ void st_fdev(void* p, size_t i, float dev) {
-        static_cast<__half*>(p)[i] = __float2half_rn(dev);
+        static_cast<__half*>(p)[i] = __float2half_rn(dev * kScale);
     }
     template <int Q>
     static __device__ __forceinline__ float ld_f(const void* p, size_t i) {
-        return t19(Q) + __half2float(static_cast<const __half*>(p)[i]);
+        return t19(Q) + ld_fdev<Q>(p, i);
     }
     template <int Q>
     static __device__ __forceinline__ void st_f(void* p, size_t i, float v) {
-        static_cast<__half*>(p)[i] = __float2half_rn(v - t19(Q));
+        st_fdev<Q>(p, i, v - t19(Q));
     }
     template <int Q>
     static __device__ __forceinline__ float ld_c(const void* p, size_t i) {
-        return __half2float(static_cast<const __half*>(p)[i]);
+        return __half2float(static_cast<const __half*>(p)[i]) * kInv;
     }
     template <int Q>
     static __device__ __forceinline__ void st_c(void* p, size_t i, float v) {
-        static_cast<__half*>(p)[i] = __float2half_rn(v);
+        static_cast<__half*>(p)[i] = __float2half_rn(v * kScale);
     }
 };
+
+// Programmatic dependent launch (sm_90+): a kernel launched with programmatic
+// stream serialization may start while the previous kernel in the stream is
+// still running. wait_prior_grid() blocks until that kernel has completed and
+// its writes are visible; allow_next_grid() lets the next kernel start its
+// blocks. Without the launch attribute both are no-ops.
+__device__ __forceinline__ void wait_prior_grid() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void allow_next_grid() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
 // Read-only load that the compiler may not merge with an earlier load of the
 // same address: re-reading a neighbour id from L1 is cheaper than keeping 18
@@ -136,48 +154,95 @@ __device__ __forceinline__ size_t write_slot_v(const DomainView& d, int n, int v
 }
 
 // ---------------------------------------------------------------------------
-// phase pass: Na, Nb -> phi (dense grid) and N (per site)          Sec. 3.1
+// component populations (D3Q7, Eqs. LBE-mass-a/b)
 // ---------------------------------------------------------------------------
-template <int PAR, class S>
-__device__ __forceinline__ void phase_site(const DomainView& d, int n, int& v, float& Na, float& Nb) {
-    v = d.site_vox[n];
-    int nb[7];
-    if constexpr (PAR == 1) {
-        static_for<1, 7>([&](auto qc) {
-            constexpr int q = decltype(qc)::value;
-            nb[q] = __ldg(d.vsite + v + d.off[q]);
-        });
+template <int PAR>
+__device__ __forceinline__ const float2* nab_prev(const DomainView& d) { return d.nab[PAR ^ 1]; }
+template <int PAR>
+__device__ __forceinline__ float2* nab_cur(const DomainView& d) { return d.nab[PAR]; }
+
+// The site that wrote slot read_slot<PAR, Q>(n) during the previous step: the
+// upstream neighbour x - xi_Q if it is a pore, else n itself (bounce-back).
+template <int Q>
+__device__ __forceinline__ int writer_of(int n, const int* nb) {
+    if constexpr (Q == 0) {
+        return n;
+    } else {
+        const int up = nb[opp(Q)];
+        return up >= 0 ? up : n;
     }
-    Na = 0.0f;
-    Nb = 0.0f;
-    static_for<0, 7>([&](auto qc) {
+}
+
+// A_q, B_q of site n at a step of parity PAR (nb[1..6]: face neighbours).
+template <int PAR, class S>
+__device__ __forceinline__ void load_components(const DomainView& d, int n, const int* nb, float (&a)[Q7],
+                                                float (&b)[Q7]) {
+    static_for<0, Q7>([&](auto qc) {
         constexpr int q = decltype(qc)::value;
         const size_t i = read_slot<PAR, q>(d, n, nb);
-        Na += S::template ld_c<q>(d.a, i);
-        Nb += S::template ld_c<q>(d.b, i);
+        a[q] = S::template ld_c<q>(d.a, i);
+        b[q] = S::template ld_c<q>(d.b, i);
+        if constexpr (S::kRef) {
+            const float2 r = __ldg(nab_prev<PAR>(d) + writer_of<q>(n, nb));
+            a[q] = fmaf(w7(q), r.x, a[q]);
+            b[q] = fmaf(w7(q), r.y, b[q]);
+        }
     });
 }
 
-__device__ __forceinline__ float phase_of(float Na, float Nb) {
-    const float Nt = Na + Nb;
-    return Nt > 0.0f ? (Na - Nb) / Nt : 0.0f;
-}
+// Whether the face-neighbour ids are needed to read the components.
+template <int PAR, class S>
+constexpr bool need_face_nb() { return PAR == 1 || S::kRef; }
 
+// ---------------------------------------------------------------------------
+// phase pass: Na, Nb -> phi (dense grid) and N (per site)          Sec. 3.1
+// ---------------------------------------------------------------------------
+// Phase pass of one site (or one periodic halo voxel mirroring a site).
+// Ordering with the neighbouring kernels under programmatic launch: only the
+// static index (site_vox, vsite) is read before wait_prior_grid(); A and B
+// (written by the previous collision) are read, and phi / nsum (read by the
+// previous collision) are written, only after it. Dependents are released
+// after the wait, so the next collision never starts before the previous
+// one has completed.
 template <int PAR, class S>
 __device__ __forceinline__ void phase_thread(const DomainView& d, int t) {
+    int n = -1, dst = -1;
     if (t < d.n_sites) {
-        int v;
-        float Na, Nb;
-        phase_site<PAR, S>(d, t, v, Na, Nb);
-        d.phi[v] = phase_of(Na, Nb);
-        d.nsum[t] = Na + Nb;
+        n = t;
     } else if (t < d.n_sites + d.n_halo) {
-        // halo voxel of a periodic face: mirror the phase of its source site
-        const int e = t - d.n_sites;
-        int v;
-        float Na, Nb;
-        phase_site<PAR, S>(d, __ldg(d.halo_site + e), v, Na, Nb);
-        d.phi[__ldg(d.halo_dst + e)] = phase_of(Na, Nb);
+        n = __ldg(d.halo_site + (t - d.n_sites));
+        dst = __ldg(d.halo_dst + (t - d.n_sites));
+    }
+    int v = 0;
+    int nb[7];
+    if (n >= 0) {
+        v = __ldg(d.site_vox + n);
+        if constexpr (need_face_nb<PAR, S>()) {
+            static_for<1, 7>([&](auto qc) {
+                constexpr int q = decltype(qc)::value;
+                nb[q] = __ldg(d.vsite + v + d.off[q]);
+            });
+        }
+    }
+    wait_prior_grid();
+    allow_next_grid();
+    if (n < 0) return;
+    float a[Q7], b[Q7];
+    load_components<PAR, S>(d, n, nb, a, b);
+    float Na = 0.0f, Nb = 0.0f;
+    static_for<0, Q7>([&](auto qc) {
+        constexpr int q = decltype(qc)::value;
+        Na += a[q];
+        Nb += b[q];
+    });
+    const float Nt = Na + Nb;
+    const float phi = Nt > 0.0f ? (Na - Nb) / Nt : 0.0f;
+    if (dst < 0) {
+        d.phi[v] = phi;
+        if constexpr (S::kRef) nab_cur<PAR>(d)[n] = make_float2(Na, Nb);
+        else d.nsum[n] = Nt;
+    } else {
+        d.phi[dst] = phi;    // halo voxel of a periodic face
     }
 }
 
@@ -206,9 +271,25 @@ __device__ __forceinline__ void collide_thread(const DomainView& d, int n) {
         f[q] = S::template ld_fdev<q>(d.f, read_slot<PAR, q>(d, n, nb));
     });
 
+    // Everything above (site and neighbour ids, f from the previous collision)
+    // is safe to read before the phase pass of this step completes; phi and
+    // nsum are its outputs, and the A/B slots written below are its inputs.
+    allow_next_grid();
+    wait_prior_grid();
+
     // phase field: own value and the 18 neighbours (solids hold phi_s)
     const float phi_c = __ldg(d.phi + v);
-    const float Nt = __ldg(d.nsum + n);
+    float Na, Nb;
+    if constexpr (S::kRef) {
+        const float2 r = __ldg(nab_cur<PAR>(d) + n);
+        Na = r.x;
+        Nb = r.y;
+    } else {
+        // Na = N (1 + phi)/2, Nb = N (1 - phi)/2 with N from the phase pass
+        const float Nt = __ldg(d.nsum + n);
+        Na = 0.5f * Nt * (1.0f + phi_c);
+        Nb = 0.5f * Nt * (1.0f - phi_c);
+    }
     float p[Q19];
     static_for<1, Q19>([&](auto qc) {
         constexpr int q = decltype(qc)::value;
@@ -224,10 +305,11 @@ __device__ __forceinline__ void collide_thread(const DomainView& d, int n) {
         if constexpr (cy(q) != 0) Cy = fmaf(g * cy(q), p[q], Cy);
         if constexpr (cz(q) != 0) Cz = fmaf(g * cz(q), p[q], Cz);
     });
-    const float Cmag = sqrtf(Cx * Cx + Cy * Cy + Cz * Cz);
-    float nx = 0.0f, ny = 0.0f, nz = 0.0f;
-    if (Cmag > 0.0f) {
-        const float inv = 1.0f / Cmag;
+    const float C2 = Cx * Cx + Cy * Cy + Cz * Cz;
+    float nx = 0.0f, ny = 0.0f, nz = 0.0f, Cmag = 0.0f;
+    if (C2 > 0.0f) {
+        const float inv = rsqrtf(C2);
+        Cmag = C2 * inv;
         nx = Cx * inv;
         ny = Cy * inv;
         nz = Cz * inv;
@@ -278,10 +360,7 @@ __device__ __forceinline__ void collide_thread(const DomainView& d, int n) {
     dma[15] = hac * nx * nz;
     const float drho_iso = drho - 1.5f * jj;
 
-    // recoloring inputs: Na = N (1 + phi)/2, Nb = N (1 - phi)/2, so the
-    // weights Nb/N and Na/N are (1 - phi)/2 and (1 + phi)/2
-    const float Na = 0.5f * Nt * (1.0f + phi_c);
-    const float Nb = 0.5f * Nt * (1.0f - phi_c);
+    // recoloring weights Nb/N and Na/N are (1 - phi)/2 and (1 + phi)/2
     const float bxa = d.beta * 0.5f * (1.0f - phi_c);
     const float bxb = d.beta * 0.5f * (1.0f + phi_c);
 
@@ -318,7 +397,9 @@ __device__ __forceinline__ void collide_thread(const DomainView& d, int n) {
 
     // recolored component distributions (Eqs. LBE-mass-a/b), streamed on the
     // fly; the rest populations take the remainder of Na and Nb so that the
-    // fp32 weights (whose sum is not exactly 1) create no mass
+    // fp32 weights (whose sum is not exactly 1) create no mass. With fp16
+    // storage the stored quantity is the deviation from w_q Na (w_q Nb), which
+    // the formula gives directly: w_q Na (4.5 u.xi + beta Nb/N n.xi).
     float asum = 0.0f, bsum = 0.0f;
     static_for<1, Q7>([&](auto qc) {
         constexpr int q = decltype(qc)::value;
@@ -326,9 +407,16 @@ __device__ __forceinline__ void collide_thread(const DomainView& d, int n) {
         if constexpr (cx(q) != 0) { ux = cx(q) * jx; nn = cx(q) * nx; }
         if constexpr (cy(q) != 0) { ux = cy(q) * jy; nn = cy(q) * ny; }
         if constexpr (cz(q) != 0) { ux = cz(q) * jz; nn = cz(q) * nz; }
-        const float base = 1.0f + 4.5f * ux;
-        const float av = w7(q) * Na * (base + bxa * nn);
-        const float bv = w7(q) * Nb * (base - bxb * nn);
+        float av, bv;
+        if constexpr (S::kRef) {
+            const float du = 4.5f * ux;
+            av = w7(q) * Na * (du + bxa * nn);
+            bv = w7(q) * Nb * (du - bxb * nn);
+        } else {
+            const float base = 1.0f + 4.5f * ux;
+            av = w7(q) * Na * (base + bxa * nn);
+            bv = w7(q) * Nb * (base - bxb * nn);
+        }
         asum += av;
         bsum += bv;
         const size_t i = write_slot_v<PAR, q>(d, n, v);
@@ -336,8 +424,13 @@ __device__ __forceinline__ void collide_thread(const DomainView& d, int n) {
         S::template st_c<q>(d.b, i, bv);
     });
     const size_t i0 = write_slot_v<PAR, 0>(d, n, v);
-    S::template st_c<0>(d.a, i0, Na - asum);
-    S::template st_c<0>(d.b, i0, Nb - bsum);
+    if constexpr (S::kRef) {
+        S::template st_c<0>(d.a, i0, -asum);
+        S::template st_c<0>(d.b, i0, -bsum);
+    } else {
+        S::template st_c<0>(d.a, i0, Na - asum);
+        S::template st_c<0>(d.b, i0, Nb - bsum);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -349,7 +442,7 @@ __device__ __forceinline__ void reservoir_thread(const DomainView& d, int n, int
                                                  float rho_out) {
     const int v = d.site_vox[n];
     int nb[Q19];
-    if constexpr (PAR == 1) {
+    if constexpr (PAR == 1 || S::kRef) {
         static_for<1, Q19>([&](auto qc) {
             constexpr int q = decltype(qc)::value;
             nb[q] = __ldg(d.vsite + v + d.off[q]);
@@ -362,8 +455,15 @@ __device__ __forceinline__ void reservoir_thread(const DomainView& d, int n, int
         const size_t i = read_slot<PAR, q>(d, n, nb);
         S::template st_f<q>(d.f, i, t19(q) * rho);
         if constexpr (q < Q7) {
-            S::template st_c<q>(d.a, i, w7(q) * na);
-            S::template st_c<q>(d.b, i, w7(q) * (1.0f - na));
+            float av = w7(q) * na, bv = w7(q) * (1.0f - na);
+            if constexpr (S::kRef) {
+                // the next step reconstructs with the writer's densities of this step
+                const float2 r = __ldg(nab_prev<PAR>(d) + writer_of<q>(n, nb));
+                av -= w7(q) * r.x;
+                bv -= w7(q) * r.y;
+            }
+            S::template st_c<q>(d.a, i, av);
+            S::template st_c<q>(d.b, i, bv);
         }
     });
 }
