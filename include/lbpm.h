@@ -267,6 +267,49 @@ lbpm_status lbpm_enable_kernel_timing(lbpm_ctx* ctx, int enable);
 lbpm_status lbpm_kernel_timing(lbpm_ctx* ctx, double* ms_collide, long long* n_collide,
                                double* ms_phase, long long* n_phase);
 
+/*
+ * Batched form: several jobs (independent contexts on one GPU, same storage
+ * precision) advanced together. Every timestep of the whole batch is ONE
+ * launch of the phase pass and ONE of the fused collide-stream kernel, both
+ * persistent over a list of tiles that covers all jobs' sites; bundles of two
+ * steps are replayed from a CUDA graph. Each job's results are bit-identical
+ * to advancing it alone. Jobs keep their own state and every per-job call
+ * (lbpm_measure, lbpm_read_field, ...) stays valid; a job joins at an even
+ * step and must be removed before it is destroyed. After changing a job's
+ * parameters, call lbpm_batch_refresh. Work runs on the batch's stream: use
+ * the same stream for the jobs, or synchronise them.
+ */
+typedef struct lbpm_batch lbpm_batch;
+
+lbpm_status lbpm_batch_create(lbpm_batch** out, int device, void* cuda_stream);
+lbpm_status lbpm_batch_destroy(lbpm_batch* batch);
+/* Allocator hooks for the batch's own tables (see lbpm_set_allocator). */
+lbpm_status lbpm_batch_set_allocator(lbpm_batch* batch, lbpm_alloc_fn alloc, lbpm_free_fn free_fn, void* user);
+const char* lbpm_batch_last_error(const lbpm_batch* batch);
+/* Add / remove a job (LBPM_E_STATE if the job has no fluids or is at an odd
+ * step; LBPM_E_INVALID for another device, another precision or a repeat). */
+lbpm_status lbpm_batch_add(lbpm_batch* batch, lbpm_ctx* job);
+lbpm_status lbpm_batch_remove(lbpm_batch* batch, lbpm_ctx* job);
+/* Re-read every job's parameters (e.g. after a body-force change). */
+lbpm_status lbpm_batch_refresh(lbpm_batch* batch);
+lbpm_status lbpm_batch_size(const lbpm_batch* batch, int* n_jobs, long long* n_sites);
+/* Advance every job by nsteps (even, asynchronous). */
+lbpm_status lbpm_batch_advance(lbpm_batch* batch, long long nsteps);
+/* Measures of every job, out[j] for the j-th job in insertion order
+ * (see lbpm_measures); LBPM_E_UNSTABLE if any job is flagged. */
+lbpm_status lbpm_batch_measure(lbpm_batch* batch, lbpm_measures* out);
+/* Launch shape: threads per block (128, 256 or 512) and resident blocks per
+ * SM of the persistent phase and collide grids (0 = occupancy limit). */
+lbpm_status lbpm_batch_set_launch(lbpm_batch* batch, int threads, int blocks_per_sm_phase,
+                                  int blocks_per_sm_collide);
+/* Autotuner: times each candidate launch shape over steps_per_candidate
+ * (even) real steps - all candidates compute identical results - keeps the
+ * fastest, and caches it per GPU, precision and size class (log2 of the
+ * batch's site count) for the process. Returns the chosen shape. */
+lbpm_status lbpm_batch_tune(lbpm_batch* batch, int steps_per_candidate, int* threads, int* blocks_per_sm_phase,
+                            int* blocks_per_sm_collide);
+lbpm_status lbpm_batch_launch_count(const lbpm_batch* batch, long long* launches);
+
 /* Number of kernel launches issued by this ctx since creation. */
 lbpm_status lbpm_launch_count(const lbpm_ctx* ctx, long long* launches);
 

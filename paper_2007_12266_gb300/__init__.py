@@ -22,7 +22,7 @@ import numpy as np
 from . import _lib
 from ._lib import LBPMError, Measures, Params
 
-__all__ = ["Domain", "LBPMError", "FIELDS", "DISTS", "library_path", "version"]
+__all__ = ["Domain", "Batch", "LBPMError", "FIELDS", "DISTS", "library_path", "version"]
 
 FIELDS = {"phi": 0, "pressure": 1, "ux": 2, "uy": 3, "uz": 4, "na": 5, "nb": 6, "rho": 7}
 DISTS = {"f": (0, 19), "a": (1, 7), "b": (2, 7)}
@@ -48,6 +48,30 @@ def _close_all():
             d.close()
         except Exception:
             pass
+
+
+def _measures_dict(m: Measures) -> dict:
+    out = {}
+    for name, _ in Measures._fields_:
+        v = getattr(m, name)
+        out[name] = list(v) if hasattr(v, "__len__") else v
+    return out
+
+
+def _torch_allocator(torch, device, stream):
+    def _alloc(nbytes, strm, user):
+        try:
+            return int(torch.cuda.caching_allocator_alloc(int(nbytes), device, stream))
+        except Exception:
+            return None
+
+    def _free(ptr, user):
+        try:
+            torch.cuda.caching_allocator_delete(int(ptr))
+        except Exception:
+            pass
+
+    return _lib.ALLOC_FN(_alloc), _lib.FREE_FN(_free)
 
 
 def _torch():
@@ -83,21 +107,7 @@ class Domain:
         _LIVE.add(self)
         self._callbacks = None
         if use_torch_allocator:
-            dev, strm = self.device, self._stream
-
-            def _alloc(nbytes, stream, user):
-                try:
-                    return int(torch.cuda.caching_allocator_alloc(int(nbytes), dev, strm))
-                except Exception:
-                    return None
-
-            def _free(ptr, user):
-                try:
-                    torch.cuda.caching_allocator_delete(int(ptr))
-                except Exception:
-                    pass
-
-            self._callbacks = (_lib.ALLOC_FN(_alloc), _lib.FREE_FN(_free))
+            self._callbacks = _torch_allocator(torch, self.device, self._stream)
             self._check(self._L.lbpm_set_allocator(self._h, self._callbacks[0], self._callbacks[1], None))
         self.set_params(tau_a=tau_a, tau_b=tau_b, alpha=alpha, beta=beta, force=force,
                         precision=precision, periodic=periodic, reservoir_z=reservoir_z,
@@ -187,11 +197,7 @@ class Domain:
         st = self._L.lbpm_measure(self._h, ct.byref(m))
         if st != 0 and (st != 5 or raise_unstable):
             self._check(st)
-        out = {}
-        for name, _ in Measures._fields_:
-            v = getattr(m, name)
-            out[name] = list(v) if hasattr(v, "__len__") else v
-        return out
+        return _measures_dict(m)
 
     # -- results ---------------------------------------------------------
     @property
@@ -267,3 +273,86 @@ class Domain:
                                                ct.byref(np_)))
         return {"collide_ms": mc.value, "collide_launches": nc.value,
                 "phase_ms": mp.value, "phase_launches": np_.value}
+
+
+class Batch:
+    """Several Domains (same GPU, same storage precision) advanced together by
+    one persistent launch per phase over all their sites (lbpm_batch_* ABI).
+    Results are bit-identical to advancing each domain alone."""
+
+    def __init__(self, device: int = 0, stream=None, use_torch_allocator: bool = True):
+        torch = _torch()
+        self._L = _lib.load()
+        self.device = int(device)
+        with torch.cuda.device(self.device):
+            self._stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        h = ct.c_void_p()
+        st = self._L.lbpm_batch_create(ct.byref(h), self.device, ct.c_void_p(self._stream.cuda_stream))
+        if st != 0:
+            raise LBPMError(st, "lbpm_batch_create failed")
+        self._h = h
+        _LIVE.add(self)
+        self._callbacks = None
+        if use_torch_allocator:
+            self._callbacks = _torch_allocator(torch, self.device, self._stream)
+            self._check(self._L.lbpm_batch_set_allocator(self._h, self._callbacks[0], self._callbacks[1], None))
+        self.jobs = []
+
+    def _check(self, status: int):
+        if status != 0:
+            raise LBPMError(status, self._L.lbpm_batch_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._L.lbpm_batch_destroy(self._h)
+            self._h = None
+            self.jobs = []
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def add(self, dom: "Domain"):
+        self._check(self._L.lbpm_batch_add(self._h, dom._h))
+        self.jobs.append(dom)
+
+    def remove(self, dom: "Domain"):
+        self._check(self._L.lbpm_batch_remove(self._h, dom._h))
+        self.jobs.remove(dom)
+
+    def refresh(self):
+        self._check(self._L.lbpm_batch_refresh(self._h))
+
+    def advance(self, nsteps: int):
+        self._check(self._L.lbpm_batch_advance(self._h, int(nsteps)))
+
+    def measure(self) -> list:
+        arr = (Measures * max(len(self.jobs), 1))()
+        st = self._L.lbpm_batch_measure(self._h, arr)
+        if st not in (0, 5):
+            self._check(st)
+        return [_measures_dict(arr[j]) for j in range(len(self.jobs))]
+
+    def set_launch(self, threads: int, blocks_per_sm_phase: int = 0, blocks_per_sm_collide: int = 0):
+        self._check(self._L.lbpm_batch_set_launch(self._h, int(threads), int(blocks_per_sm_phase),
+                                                  int(blocks_per_sm_collide)))
+
+    def tune(self, steps_per_candidate: int = 4):
+        t, p, c = ct.c_int(), ct.c_int(), ct.c_int()
+        self._check(self._L.lbpm_batch_tune(self._h, int(steps_per_candidate), ct.byref(t), ct.byref(p),
+                                            ct.byref(c)))
+        return t.value, p.value, c.value
+
+    @property
+    def n_sites(self) -> int:
+        n, s = ct.c_int(), ct.c_longlong()
+        self._check(self._L.lbpm_batch_size(self._h, ct.byref(n), ct.byref(s)))
+        return s.value
+
+    @property
+    def launch_count(self) -> int:
+        n = ct.c_longlong()
+        self._check(self._L.lbpm_batch_launch_count(self._h, ct.byref(n)))
+        return n.value

@@ -76,6 +76,20 @@ SIGNATURES = {
     "lbpm_kernel_timing": (ct.c_int, [c_ctx_p, ct.POINTER(ct.c_double), ct.POINTER(ct.c_longlong),
                                       ct.POINTER(ct.c_double), ct.POINTER(ct.c_longlong)]),
     "lbpm_launch_count": (ct.c_int, [c_ctx_p, ct.POINTER(ct.c_longlong)]),
+    "lbpm_batch_create": (ct.c_int, [ct.POINTER(ct.c_void_p), ct.c_int, ct.c_void_p]),
+    "lbpm_batch_destroy": (ct.c_int, [ct.c_void_p]),
+    "lbpm_batch_set_allocator": (ct.c_int, [ct.c_void_p, ALLOC_FN, FREE_FN, ct.c_void_p]),
+    "lbpm_batch_last_error": (ct.c_char_p, [ct.c_void_p]),
+    "lbpm_batch_add": (ct.c_int, [ct.c_void_p, c_ctx_p]),
+    "lbpm_batch_remove": (ct.c_int, [ct.c_void_p, c_ctx_p]),
+    "lbpm_batch_refresh": (ct.c_int, [ct.c_void_p]),
+    "lbpm_batch_size": (ct.c_int, [ct.c_void_p, ct.POINTER(ct.c_int), ct.POINTER(ct.c_longlong)]),
+    "lbpm_batch_advance": (ct.c_int, [ct.c_void_p, ct.c_longlong]),
+    "lbpm_batch_measure": (ct.c_int, [ct.c_void_p, ct.c_void_p]),
+    "lbpm_batch_set_launch": (ct.c_int, [ct.c_void_p, ct.c_int, ct.c_int, ct.c_int]),
+    "lbpm_batch_tune": (ct.c_int, [ct.c_void_p, ct.c_int, ct.POINTER(ct.c_int), ct.POINTER(ct.c_int),
+                                   ct.POINTER(ct.c_int)]),
+    "lbpm_batch_launch_count": (ct.c_int, [ct.c_void_p, ct.POINTER(ct.c_longlong)]),
 }
 
 _lib = None

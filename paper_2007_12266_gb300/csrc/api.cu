@@ -279,6 +279,44 @@ void dfree(lbpm_ctx* c, void* p) {
 
 }  // namespace lbm
 
+namespace lbm {
+
+// Measures of Sec. 4 / Sec. 3.4 from the NSUM device sums of one domain.
+void fill_measures(const lbpm_ctx* c, const double* S, lbpm_measures* out) {
+    std::memset(out, 0, sizeof *out);
+    const double N = static_cast<double>(c->N), V = static_cast<double>(c->V);
+    const double cnt_a = S[3], cnt_b = N - S[3];
+    out->step = c->step;
+    out->n_sites = c->N;
+    out->sat_mass = (S[0] + S[1]) > 0 ? S[0] / (S[0] + S[1]) : 0.0;
+    out->sat_count = N > 0 ? cnt_a / N : 0.0;
+    out->mass_a = S[0];
+    out->mass_b = S[1];
+    out->mass_total = S[2];
+    for (int a = 0; a < 3; ++a) {
+        out->flux[a] = S[4 + a] / V;
+        out->flux_a[a] = S[7 + a] / V;
+        out->flux_b[a] = S[10 + a] / V;
+        out->mom_a[a] = S[15 + a];
+        out->mom_b[a] = S[18 + a];
+    }
+    out->ke_a = S[21];
+    out->ke_b = S[22];
+    out->p_a = cnt_a > 0 ? S[23] / cnt_a : 0.0;
+    out->p_b = cnt_b > 0 ? S[24] / cnt_b : 0.0;
+    out->vol_a = cnt_a;
+    out->vol_b = cnt_b;
+    if (c->params.alpha > 0.0) {
+        const double mu_a = (c->params.tau_a - 0.5) / 3.0, mu_b = (c->params.tau_b - 0.5) / 3.0;
+        const double ua = S[13] > 0 ? std::sqrt(S[15] * S[15] + S[16] * S[16] + S[17] * S[17]) / S[13] : 0.0;
+        const double ub = S[14] > 0 ? std::sqrt(S[18] * S[18] + S[19] * S[19] + S[20] * S[20]) / S[14] : 0.0;
+        out->ca = ((cnt_a / V) * mu_a * ua + (cnt_b / V) * mu_b * ub) / (6.0 * c->params.alpha);
+    }
+    out->status = (S[25] > 0 ? 1 : 0) | (S[26] > 0 ? 2 : 0);
+}
+
+}  // namespace lbm
+
 extern "C" {
 
 const char* lbpm_version(void) { return "lbpm-gb300 0.1 (sm_103a)"; }
@@ -560,36 +598,7 @@ lbpm_status lbpm_measure(lbpm_ctx* c, lbpm_measures* out) {
     dfree(c, d_out);
     if (e != cudaSuccess) return fail_cuda(c, "measure", e);
     c->launches += 2;
-    std::memset(out, 0, sizeof *out);
-    const double N = static_cast<double>(c->N), V = static_cast<double>(c->V);
-    const double cnt_a = S[3], cnt_b = N - S[3];
-    out->step = c->step;
-    out->n_sites = c->N;
-    out->sat_mass = (S[0] + S[1]) > 0 ? S[0] / (S[0] + S[1]) : 0.0;
-    out->sat_count = N > 0 ? cnt_a / N : 0.0;
-    out->mass_a = S[0];
-    out->mass_b = S[1];
-    out->mass_total = S[2];
-    for (int a = 0; a < 3; ++a) {
-        out->flux[a] = S[4 + a] / V;
-        out->flux_a[a] = S[7 + a] / V;
-        out->flux_b[a] = S[10 + a] / V;
-        out->mom_a[a] = S[15 + a];
-        out->mom_b[a] = S[18 + a];
-    }
-    out->ke_a = S[21];
-    out->ke_b = S[22];
-    out->p_a = cnt_a > 0 ? S[23] / cnt_a : 0.0;
-    out->p_b = cnt_b > 0 ? S[24] / cnt_b : 0.0;
-    out->vol_a = cnt_a;
-    out->vol_b = cnt_b;
-    if (c->params.alpha > 0.0) {
-        const double mu_a = (c->params.tau_a - 0.5) / 3.0, mu_b = (c->params.tau_b - 0.5) / 3.0;
-        const double ua = S[13] > 0 ? std::sqrt(S[15] * S[15] + S[16] * S[16] + S[17] * S[17]) / S[13] : 0.0;
-        const double ub = S[14] > 0 ? std::sqrt(S[18] * S[18] + S[19] * S[19] + S[20] * S[20]) / S[14] : 0.0;
-        out->ca = ((cnt_a / V) * mu_a * ua + (cnt_b / V) * mu_b * ub) / (6.0 * c->params.alpha);
-    }
-    out->status = (S[25] > 0 ? 1 : 0) | (S[26] > 0 ? 2 : 0);
+    fill_measures(c, S, out);
     if (out->status) {
         c->unstable = true;
         return fail(c, LBPM_E_UNSTABLE, "non-finite or negative densities in the state");

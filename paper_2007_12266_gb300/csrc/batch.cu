@@ -1,0 +1,183 @@
+// Batched form: many independent domains (jobs) advanced together.
+//
+// Each job keeps its own context and device arrays. A batch builds a device
+// table of the jobs' views and a global list of tiles (job, first thread) over
+// all jobs, and advances every job with ONE persistent launch per phase: the
+// blocks of the phase kernel, then of the fused collide-stream kernel, walk
+// the whole tile list in a fixed round-robin order. Step bundles are captured
+// into a CUDA graph. Bundles hold an even number of steps, so every job is at
+// an even step at a bundle boundary and the AA parity of each launch is a
+// compile-time constant for the whole batch.
+//
+// The launch shape (threads per block, resident blocks per SM) is picked by a
+// small autotuner that times candidates on real steps (every candidate
+// computes identical results, so tuning advances the simulation normally) and
+// caches the winner per GPU, precision and size class.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "measure_kernels.cuh"
+
+namespace lbm {
+
+
+namespace {
+
+constexpr int kMaxBlocksPerSm = 16;
+
+template <int PAR, class S, int BT>
+__global__ void __launch_bounds__(BT) k_batch_phase(const DomainView* views, const BatchTile* tiles, int n_tiles) {
+    __shared__ DomainView sv;
+    for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+        const BatchTile tl = tiles[t];
+        if (threadIdx.x < static_cast<int>(sizeof(DomainView) / sizeof(int)))
+            reinterpret_cast<int*>(&sv)[threadIdx.x] = reinterpret_cast<const int*>(views + tl.job)[threadIdx.x];
+        __syncthreads();
+        phase_thread<PAR, S>(sv, tl.first + threadIdx.x);
+        __syncthreads();
+    }
+}
+
+template <int PAR, class S, int BT>
+__global__ void __launch_bounds__(BT) k_batch_collide(const DomainView* views, const BatchTile* tiles, int n_tiles) {
+    __shared__ DomainView sv;
+    for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+        const BatchTile tl = tiles[t];
+        if (threadIdx.x < static_cast<int>(sizeof(DomainView) / sizeof(int)))
+            reinterpret_cast<int*>(&sv)[threadIdx.x] = reinterpret_cast<const int*>(views + tl.job)[threadIdx.x];
+        __syncthreads();
+        const int n = tl.first + threadIdx.x;
+        if (n < sv.n_sites) collide_thread<PAR, S>(sv, n);
+        __syncthreads();
+    }
+}
+
+static_assert(sizeof(DomainView) % sizeof(int) == 0, "view copied as ints");
+
+template <int BT>
+struct Launch {
+    template <class K>
+    static cudaError_t go(K kernel, unsigned grid, cudaStream_t s, const DomainView* v, const BatchTile* t, int nt) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(grid);
+        cfg.blockDim = dim3(BT);
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        return cudaLaunchKernelEx(&cfg, kernel, v, t, nt);
+    }
+};
+
+template <int BT>
+cudaError_t batch_phase_bt(int par, bool fp16, unsigned grid, cudaStream_t s, const DomainView* v,
+                           const BatchTile* t, int nt) {
+    if (par == 0)
+        return fp16 ? Launch<BT>::go(k_batch_phase<0, StoreF16, BT>, grid, s, v, t, nt)
+                    : Launch<BT>::go(k_batch_phase<0, StoreF32, BT>, grid, s, v, t, nt);
+    return fp16 ? Launch<BT>::go(k_batch_phase<1, StoreF16, BT>, grid, s, v, t, nt)
+                : Launch<BT>::go(k_batch_phase<1, StoreF32, BT>, grid, s, v, t, nt);
+}
+
+template <int BT>
+cudaError_t batch_collide_bt(int par, bool fp16, unsigned grid, cudaStream_t s, const DomainView* v,
+                             const BatchTile* t, int nt) {
+    if (par == 0)
+        return fp16 ? Launch<BT>::go(k_batch_collide<0, StoreF16, BT>, grid, s, v, t, nt)
+                    : Launch<BT>::go(k_batch_collide<0, StoreF32, BT>, grid, s, v, t, nt);
+    return fp16 ? Launch<BT>::go(k_batch_collide<1, StoreF16, BT>, grid, s, v, t, nt)
+                : Launch<BT>::go(k_batch_collide<1, StoreF32, BT>, grid, s, v, t, nt);
+}
+
+}  // namespace
+
+// Launch one phase (0 = phase pass, 1 = collide-stream) over all tiles.
+cudaError_t launch_batch(int kernel, int par, bool fp16, int bt, unsigned grid, cudaStream_t s,
+                         const DomainView* v, const BatchTile* t, int nt) {
+    if (nt == 0) return cudaSuccess;
+    switch (bt) {
+    case 128: return kernel == 0 ? batch_phase_bt<128>(par, fp16, grid, s, v, t, nt)
+                                 : batch_collide_bt<128>(par, fp16, grid, s, v, t, nt);
+    case 512: return kernel == 0 ? batch_phase_bt<512>(par, fp16, grid, s, v, t, nt)
+                                 : batch_collide_bt<512>(par, fp16, grid, s, v, t, nt);
+    default: return kernel == 0 ? batch_phase_bt<256>(par, fp16, grid, s, v, t, nt)
+                                : batch_collide_bt<256>(par, fp16, grid, s, v, t, nt);
+    }
+}
+
+namespace {
+
+// Per-tile fp64 partial sums of the measures; each job's parity is read per tile.
+template <class S, int BT>
+__global__ void __launch_bounds__(BT) k_batch_measure(const DomainView* views, const int* parity,
+                                                      const BatchTile* tiles, int n_tiles, double* partials) {
+    __shared__ DomainView sv;
+    __shared__ int par;
+    for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+        const BatchTile tl = tiles[t];
+        if (threadIdx.x < static_cast<int>(sizeof(DomainView) / sizeof(int)))
+            reinterpret_cast<int*>(&sv)[threadIdx.x] = reinterpret_cast<const int*>(views + tl.job)[threadIdx.x];
+        if (threadIdx.x == 0) par = parity[tl.job];
+        __syncthreads();
+        Acc2 acc[NSUM];
+        const int n = tl.first + threadIdx.x;
+        if (n < sv.n_sites) {
+            if (par) measure_site<1, S>(sv, n, acc);
+            else measure_site<0, S>(sv, n, acc);
+        }
+        block_reduce_sums<BT>(acc, partials + static_cast<size_t>(t) * NSUM);
+    }
+}
+
+// One block per job, one warp per quantity: fixed-order sum of the job's tiles.
+__global__ void k_batch_job_reduce(const double* partials, const int* tile_begin, int n_jobs, double* out) {
+    const int j = blockIdx.x;
+    const int i = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (j >= n_jobs || i >= NSUM) return;
+    double s = 0.0;
+    for (int t = tile_begin[j] + lane; t < tile_begin[j + 1]; t += 32) s += partials[static_cast<size_t>(t) * NSUM + i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) out[static_cast<size_t>(j) * NSUM + i] = s;
+}
+
+}  // namespace
+
+cudaError_t launch_batch_measure(bool fp16, unsigned grid, cudaStream_t s, const DomainView* v, const int* parity,
+                                 const BatchTile* t, int nt, double* partials, const int* tile_begin, int n_jobs,
+                                 double* out) {
+    if (nt > 0) {
+        if (fp16) k_batch_measure<StoreF16, 256><<<grid, 256, 0, s>>>(v, parity, t, nt, partials);
+        else k_batch_measure<StoreF32, 256><<<grid, 256, 0, s>>>(v, parity, t, nt, partials);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    if (n_jobs > 0) k_batch_job_reduce<<<n_jobs, 32 * NSUM, 0, s>>>(partials, tile_begin, n_jobs, out);
+    return cudaGetLastError();
+}
+
+// Resident blocks per SM of a batch kernel at a block size (occupancy limit).
+int batch_max_blocks(int kernel, bool fp16, int bt) {
+    int nb = 0;
+    const void* f = nullptr;
+#define LBPM_PICK(BT)                                                                                        \
+    f = kernel == 0 ? (fp16 ? (const void*)k_batch_phase<1, StoreF16, BT> : (const void*)k_batch_phase<1, StoreF32, BT>) \
+                    : (fp16 ? (const void*)k_batch_collide<1, StoreF16, BT>                                   \
+                            : (const void*)k_batch_collide<1, StoreF32, BT>);
+    if (bt == 128) { LBPM_PICK(128) } else if (bt == 512) { LBPM_PICK(512) } else { LBPM_PICK(256) }
+#undef LBPM_PICK
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f, bt, 0) != cudaSuccess) {
+        cudaGetLastError();
+        return 1;
+    }
+    return std::max(1, std::min(nb, kMaxBlocksPerSm));
+}
+
+}  // namespace lbm

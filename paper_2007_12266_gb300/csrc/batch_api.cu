@@ -1,0 +1,435 @@
+// C ABI of the batched form (declared in include/lbpm.h): a batch of job
+// contexts advanced together by the persistent batch kernels (batch.cu).
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+using namespace lbm;
+
+struct lbpm_batch {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    std::string err;
+    lbpm_alloc_fn alloc = nullptr;
+    lbpm_free_fn free_fn = nullptr;
+    void* alloc_user = nullptr;
+    std::vector<lbpm_ctx*> jobs;
+    int precision = -1;
+    // device tables
+    DomainView* d_views = nullptr;
+    int* d_parity = nullptr;
+    BatchTile* d_tiles[2] = {nullptr, nullptr};  // phase, collide (tile = bt threads)
+    BatchTile* d_mtiles = nullptr;               // measure tiles (256 sites)
+    int* d_mbegin = nullptr;                     // [J+1] first measure tile of each job
+    double* d_partials = nullptr;
+    double* d_out = nullptr;
+    size_t cap_views = 0, cap_tiles[2] = {0, 0}, cap_mtiles = 0;
+    int n_tiles[2] = {0, 0};
+    int n_mtiles = 0;
+    bool dirty = true;
+    // launch shape
+    int bt = 256;
+    int bps[2] = {0, 0};   // resident blocks per SM used for the persistent grids (0 = occupancy limit)
+    int n_sm = 0;
+    // bundle graph (2 timesteps)
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t graph = nullptr;
+    long long launches = 0;
+};
+
+namespace {
+
+lbpm_status bfail(lbpm_batch* b, lbpm_status s, const std::string& m) {
+    if (b) b->err = m;
+    return s;
+}
+
+lbpm_status bfail_cuda(lbpm_batch* b, const char* what, cudaError_t e) {
+    return bfail(b, e == cudaErrorMemoryAllocation ? LBPM_E_OOM : LBPM_E_CUDA,
+                 std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")");
+}
+
+#define LBPM_BCK(b, call)                                          \
+    do {                                                           \
+        cudaError_t e_ = (call);                                   \
+        if (e_ != cudaSuccess) return bfail_cuda(b, #call, e_);    \
+    } while (0)
+
+void* balloc(lbpm_batch* b, size_t bytes) {
+    void* p = nullptr;
+    if (b->alloc) return b->alloc(bytes ? bytes : 16, b->stream, b->alloc_user);
+    if (cudaMalloc(&p, bytes ? bytes : 16) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return p;
+}
+
+void bfree(lbpm_batch* b, void* p) {
+    if (!p) return;
+    if (b->free_fn) b->free_fn(p, b->alloc_user);
+    else cudaFree(p);
+}
+
+template <class T>
+bool ensure(lbpm_batch* b, T** p, size_t* cap, size_t n) {
+    if (*p && *cap >= n) return true;
+    bfree(b, *p);
+    const size_t c = std::max<size_t>(n, 16) * 3 / 2;
+    *p = static_cast<T*>(balloc(b, sizeof(T) * c));
+    *cap = *p ? c : 0;
+    return *p != nullptr;
+}
+
+void drop_graph(lbpm_batch* b) {
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+}
+
+lbpm_status enter(lbpm_batch* b) {
+    if (!b) return LBPM_E_INVALID;
+    b->err.clear();
+    cudaError_t e = cudaSetDevice(b->device);
+    if (e != cudaSuccess) return bfail_cuda(b, "cudaSetDevice", e);
+    return LBPM_OK;
+}
+
+// (Re)build the device job table and tile lists.
+lbpm_status rebuild(lbpm_batch* b) {
+    drop_graph(b);
+    const int J = static_cast<int>(b->jobs.size());
+    std::vector<DomainView> views(J);
+    std::vector<int> parity(J);
+    std::vector<BatchTile> tiles[2];
+    std::vector<BatchTile> mtiles;
+    std::vector<int> mbegin(J + 1, 0);
+    for (int j = 0; j < J; ++j) {
+        const lbpm_ctx* c = b->jobs[j];
+        views[j] = make_view(c);
+        parity[j] = static_cast<int>(c->step & 1);
+        const long long counts[2] = {c->N + c->H, c->N};
+        for (int k = 0; k < 2; ++k)
+            for (long long f = 0; f < counts[k]; f += b->bt) tiles[k].push_back(BatchTile{j, static_cast<int>(f)});
+        mbegin[j] = static_cast<int>(mtiles.size());
+        for (long long f = 0; f < c->N; f += 256) mtiles.push_back(BatchTile{j, static_cast<int>(f)});
+    }
+    mbegin[J] = static_cast<int>(mtiles.size());
+    if (!ensure(b, &b->d_views, &b->cap_views, J)) return bfail(b, LBPM_E_OOM, "batch table allocation failed");
+    // parity, measure-begin, partials and outputs are re-allocated to fit
+    bfree(b, b->d_parity);
+    bfree(b, b->d_mbegin);
+    bfree(b, b->d_partials);
+    bfree(b, b->d_out);
+    b->d_parity = static_cast<int*>(balloc(b, sizeof(int) * std::max(J, 1)));
+    b->d_mbegin = static_cast<int*>(balloc(b, sizeof(int) * (J + 1)));
+    b->d_partials = static_cast<double*>(balloc(b, sizeof(double) * NSUM * std::max<size_t>(mtiles.size(), 1)));
+    b->d_out = static_cast<double*>(balloc(b, sizeof(double) * NSUM * std::max(J, 1)));
+    if (!b->d_parity || !b->d_mbegin || !b->d_partials || !b->d_out)
+        return bfail(b, LBPM_E_OOM, "batch table allocation failed");
+    for (int k = 0; k < 2; ++k)
+        if (!ensure(b, &b->d_tiles[k], &b->cap_tiles[k], tiles[k].size()))
+            return bfail(b, LBPM_E_OOM, "batch tile allocation failed");
+    if (!ensure(b, &b->d_mtiles, &b->cap_mtiles, mtiles.size()))
+        return bfail(b, LBPM_E_OOM, "batch tile allocation failed");
+    if (J) {
+        LBPM_BCK(b, cudaMemcpyAsync(b->d_views, views.data(), sizeof(DomainView) * J, cudaMemcpyHostToDevice, b->stream));
+        LBPM_BCK(b, cudaMemcpyAsync(b->d_parity, parity.data(), sizeof(int) * J, cudaMemcpyHostToDevice, b->stream));
+    }
+    LBPM_BCK(b, cudaMemcpyAsync(b->d_mbegin, mbegin.data(), sizeof(int) * (J + 1), cudaMemcpyHostToDevice, b->stream));
+    for (int k = 0; k < 2; ++k) {
+        b->n_tiles[k] = static_cast<int>(tiles[k].size());
+        if (b->n_tiles[k])
+            LBPM_BCK(b, cudaMemcpyAsync(b->d_tiles[k], tiles[k].data(), sizeof(BatchTile) * tiles[k].size(),
+                                        cudaMemcpyHostToDevice, b->stream));
+    }
+    b->n_mtiles = static_cast<int>(mtiles.size());
+    if (b->n_mtiles)
+        LBPM_BCK(b, cudaMemcpyAsync(b->d_mtiles, mtiles.data(), sizeof(BatchTile) * mtiles.size(),
+                                    cudaMemcpyHostToDevice, b->stream));
+    LBPM_BCK(b, cudaStreamSynchronize(b->stream));
+    b->dirty = false;
+    return LBPM_OK;
+}
+
+unsigned grid_for(const lbpm_batch* b, int k) {
+    const int occ = batch_max_blocks(k, b->precision == LBPM_FP16, b->bt);
+    const int bps = b->bps[k] > 0 ? std::min(b->bps[k], occ) : occ;
+    const long long persistent = static_cast<long long>(bps) * b->n_sm;
+    return static_cast<unsigned>(std::max<long long>(1, std::min<long long>(persistent, b->n_tiles[k])));
+}
+
+cudaError_t enqueue_step(lbpm_batch* b, int par, cudaStream_t s) {
+    const bool h = b->precision == LBPM_FP16;
+    cudaError_t e = launch_batch(0, par, h, b->bt, grid_for(b, 0), s, b->d_views, b->d_tiles[0], b->n_tiles[0]);
+    if (e == cudaSuccess)
+        e = launch_batch(1, par, h, b->bt, grid_for(b, 1), s, b->d_views, b->d_tiles[1], b->n_tiles[1]);
+    for (lbpm_ctx* c : b->jobs)
+        if (e == cudaSuccess && c->n_slab) e = launch_reservoir(c, par ^ 1, s);
+    return e;
+}
+
+lbpm_status capture(lbpm_batch* b) {
+    drop_graph(b);
+    if (!b->cap_stream) LBPM_BCK(b, cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking));
+    LBPM_BCK(b, cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t el = enqueue_step(b, 0, b->cap_stream);
+    if (el == cudaSuccess) el = enqueue_step(b, 1, b->cap_stream);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(b->cap_stream, &g);
+    if (el != cudaSuccess) e = el;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->graph, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) return bfail_cuda(b, "batch graph capture", e);
+    return LBPM_OK;
+}
+
+int kernels_per_bundle(const lbpm_batch* b) {
+    int k = 4;
+    for (const lbpm_ctx* c : b->jobs) k += c->n_slab ? 2 : 0;
+    return k;
+}
+
+// launch-shape cache: (gpu, precision, log2 of the site count) -> (bt, bps0, bps1)
+std::mutex g_tune_mu;
+std::map<std::string, std::vector<int>> g_tune_cache;
+
+std::string tune_key(const lbpm_batch* b) {
+    cudaDeviceProp p{};
+    cudaGetDeviceProperties(&p, b->device);
+    long long n = 0;
+    for (const lbpm_ctx* c : b->jobs) n += c->N;
+    int lg = 0;
+    while ((1LL << (lg + 1)) <= n) ++lg;
+    return std::string(p.name) + "/" + std::to_string(b->precision) + "/" + std::to_string(lg);
+}
+
+}  // namespace
+
+extern "C" {
+
+lbpm_status lbpm_batch_create(lbpm_batch** out, int device, void* cuda_stream) {
+    if (!out) return LBPM_E_INVALID;
+    *out = nullptr;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) {
+        cudaGetLastError();
+        return LBPM_E_INVALID;
+    }
+    if (cudaSetDevice(device) != cudaSuccess) return LBPM_E_CUDA;
+    lbpm_batch* b = new (std::nothrow) lbpm_batch();
+    if (!b) return LBPM_E_OOM;
+    b->device = device;
+    b->stream = static_cast<cudaStream_t>(cuda_stream);
+    cudaDeviceGetAttribute(&b->n_sm, cudaDevAttrMultiProcessorCount, device);
+    *out = b;
+    return LBPM_OK;
+}
+
+lbpm_status lbpm_batch_destroy(lbpm_batch* b) {
+    if (!b) return LBPM_OK;
+    cudaSetDevice(b->device);
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    else cudaDeviceSynchronize();
+    drop_graph(b);
+    if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+    bfree(b, b->d_views);
+    bfree(b, b->d_parity);
+    bfree(b, b->d_tiles[0]);
+    bfree(b, b->d_tiles[1]);
+    bfree(b, b->d_mtiles);
+    bfree(b, b->d_mbegin);
+    bfree(b, b->d_partials);
+    bfree(b, b->d_out);
+    delete b;
+    return LBPM_OK;
+}
+
+lbpm_status lbpm_batch_set_allocator(lbpm_batch* b, lbpm_alloc_fn alloc, lbpm_free_fn free_fn, void* user) {
+    if (!b) return LBPM_E_INVALID;
+    if (b->d_views) return bfail(b, LBPM_E_STATE, "set the allocator before adding jobs");
+    if (alloc && !free_fn) return bfail(b, LBPM_E_INVALID, "an allocator needs a free function");
+    b->alloc = alloc;
+    b->free_fn = alloc ? free_fn : nullptr;
+    b->alloc_user = user;
+    return LBPM_OK;
+}
+
+const char* lbpm_batch_last_error(const lbpm_batch* b) { return b ? b->err.c_str() : ""; }
+
+lbpm_status lbpm_batch_add(lbpm_batch* b, lbpm_ctx* job) {
+    lbpm_status s = enter(b);
+    if (s) return s;
+    if (!job) return bfail(b, LBPM_E_INVALID, "job is NULL");
+    if (job->device != b->device) return bfail(b, LBPM_E_INVALID, "job lives on another device");
+    if (!job->have_fluids) return bfail(b, LBPM_E_STATE, "initialise the job's fluids first");
+    if (job->step & 1) return bfail(b, LBPM_E_STATE, "a job joins a batch at an even step");
+    if (std::find(b->jobs.begin(), b->jobs.end(), job) != b->jobs.end())
+        return bfail(b, LBPM_E_INVALID, "job is already in the batch");
+    if (b->precision >= 0 && job->params.precision != b->precision)
+        return bfail(b, LBPM_E_INVALID, "all jobs of a batch share the storage precision");
+    if (job->N + job->H >= (1LL << 31)) return bfail(b, LBPM_E_INVALID, "job too large");
+    // the job's pending work (on its own stream) must be done before the batch uses it
+    if (cudaStreamSynchronize(job->stream) != cudaSuccess) return bfail(b, LBPM_E_CUDA, "job stream failed");
+    b->precision = job->params.precision;
+    b->jobs.push_back(job);
+    b->dirty = true;
+    return LBPM_OK;
+}
+
+lbpm_status lbpm_batch_remove(lbpm_batch* b, lbpm_ctx* job) {
+    lbpm_status s = enter(b);
+    if (s) return s;
+    auto it = std::find(b->jobs.begin(), b->jobs.end(), job);
+    if (it == b->jobs.end()) return bfail(b, LBPM_E_INVALID, "job is not in the batch");
+    LBPM_BCK(b, cudaStreamSynchronize(b->stream));
+    b->jobs.erase(it);
+    if (b->jobs.empty()) b->precision = -1;
+    b->dirty = true;
+    return LBPM_OK;
+}
+
+lbpm_status lbpm_batch_refresh(lbpm_batch* b) {
+    lbpm_status s = enter(b);
+    if (s) return s;
+    LBPM_BCK(b, cudaStreamSynchronize(b->stream));
+    b->dirty = true;
+    return LBPM_OK;
+}
+
+lbpm_status lbpm_batch_size(const lbpm_batch* b, int* n_jobs, long long* n_sites) {
+    if (!b) return LBPM_E_INVALID;
+    if (n_jobs) *n_jobs = static_cast<int>(b->jobs.size());
+    if (n_sites) {
+        long long n = 0;
+        for (const lbpm_ctx* c : b->jobs) n += c->N;
+        *n_sites = n;
+    }
+    return LBPM_OK;
+}
+
+lbpm_status lbpm_batch_advance(lbpm_batch* b, long long nsteps) {
+    lbpm_status s = enter(b);
+    if (s) return s;
+    if (nsteps < 0 || (nsteps & 1)) return bfail(b, LBPM_E_INVALID, "nsteps must be even and >= 0");
+    for (lbpm_ctx* c : b->jobs) {
+        if (c->unstable) return bfail(b, LBPM_E_UNSTABLE, "a job was flagged unstable");
+        if (c->step & 1) return bfail(b, LBPM_E_STATE, "a job was advanced to an odd step outside the batch");
+    }
+    if (b->jobs.empty() || nsteps == 0) return LBPM_OK;
+    if (b->dirty && (s = rebuild(b))) return s;
+    if (!b->graph && (s = capture(b))) return s;
+    for (long long k = 0; k < nsteps; k += 2) LBPM_BCK(b, cudaGraphLaunch(b->graph, b->stream));
+    b->launches += (nsteps / 2) * kernels_per_bundle(b);
+    for (lbpm_ctx* c : b->jobs) c->step += nsteps;
+    return LBPM_OK;
+}
+
+lbpm_status lbpm_batch_measure(lbpm_batch* b, lbpm_measures* out) {
+    lbpm_status s = enter(b);
+    if (s) return s;
+    if (!out) return bfail(b, LBPM_E_INVALID, "out is NULL");
+    const int J = static_cast<int>(b->jobs.size());
+    if (!J) return LBPM_OK;
+    if (b->dirty && (s = rebuild(b))) return s;
+    std::vector<int> parity(J);
+    for (int j = 0; j < J; ++j) parity[j] = static_cast<int>(b->jobs[j]->step & 1);
+    LBPM_BCK(b, cudaMemcpyAsync(b->d_parity, parity.data(), sizeof(int) * J, cudaMemcpyHostToDevice, b->stream));
+    const unsigned grid = static_cast<unsigned>(std::max(1, std::min(b->n_mtiles, 4 * b->n_sm)));
+    LBPM_BCK(b, launch_batch_measure(b->precision == LBPM_FP16, grid, b->stream, b->d_views, b->d_parity,
+                                     b->d_mtiles, b->n_mtiles, b->d_partials, b->d_mbegin, J, b->d_out));
+    std::vector<double> S(static_cast<size_t>(NSUM) * J);
+    LBPM_BCK(b, cudaMemcpyAsync(S.data(), b->d_out, sizeof(double) * S.size(), cudaMemcpyDeviceToHost, b->stream));
+    LBPM_BCK(b, cudaStreamSynchronize(b->stream));
+    b->launches += 2;
+    lbpm_status st = LBPM_OK;
+    for (int j = 0; j < J; ++j) {
+        fill_measures(b->jobs[j], S.data() + static_cast<size_t>(NSUM) * j, out + j);
+        if (out[j].status) {
+            b->jobs[j]->unstable = true;
+            st = LBPM_E_UNSTABLE;
+        }
+    }
+    if (st) return bfail(b, st, "a job has non-finite values or a blown-up density");
+    return LBPM_OK;
+}
+
+lbpm_status lbpm_batch_set_launch(lbpm_batch* b, int threads, int bps_phase, int bps_collide) {
+    lbpm_status s = enter(b);
+    if (s) return s;
+    if (threads != 128 && threads != 256 && threads != 512)
+        return bfail(b, LBPM_E_INVALID, "threads per block must be 128, 256 or 512");
+    if (bps_phase < 0 || bps_collide < 0) return bfail(b, LBPM_E_INVALID, "blocks per SM must be >= 0");
+    LBPM_BCK(b, cudaStreamSynchronize(b->stream));
+    if (threads != b->bt) b->dirty = true;
+    b->bt = threads;
+    b->bps[0] = bps_phase;
+    b->bps[1] = bps_collide;
+    drop_graph(b);
+    return LBPM_OK;
+}
+
+lbpm_status lbpm_batch_tune(lbpm_batch* b, int steps_per_candidate, int* threads, int* bps_phase, int* bps_collide) {
+    lbpm_status s = enter(b);
+    if (s) return s;
+    if (b->jobs.empty()) return bfail(b, LBPM_E_STATE, "the batch has no job");
+    if (steps_per_candidate < 2 || (steps_per_candidate & 1))
+        return bfail(b, LBPM_E_INVALID, "steps_per_candidate must be even and >= 2");
+    const std::string key = tune_key(b);
+    std::vector<int> best;
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) best = it->second;
+    }
+    if (best.empty()) {
+        cudaEvent_t e0, e1;
+        LBPM_BCK(b, cudaEventCreate(&e0));
+        LBPM_BCK(b, cudaEventCreate(&e1));
+        float best_ms = 1e30f;
+        const bool h = b->precision == LBPM_FP16;
+        for (int bt : {128, 256, 512}) {
+            const int occ = std::min(batch_max_blocks(0, h, bt), batch_max_blocks(1, h, bt));
+            for (int frac : {4, 2, 1}) {  // occupancy limit, half of it, a quarter
+                const int bps = std::max(1, occ * frac / 4);
+                if ((s = lbpm_batch_set_launch(b, bt, bps, bps))) break;
+                if ((s = lbpm_batch_advance(b, 2))) break;  // capture + warm up
+                cudaEventRecord(e0, b->stream);
+                if ((s = lbpm_batch_advance(b, steps_per_candidate))) break;
+                cudaEventRecord(e1, b->stream);
+                cudaEventSynchronize(e1);
+                float ms = 0.0f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (ms < best_ms) {
+                    best_ms = ms;
+                    best = {bt, bps, bps};
+                }
+            }
+            if (s) break;
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        if (s) return s;
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        g_tune_cache[key] = best;
+    }
+    if ((s = lbpm_batch_set_launch(b, best[0], best[1], best[2]))) return s;
+    if (threads) *threads = best[0];
+    if (bps_phase) *bps_phase = best[1];
+    if (bps_collide) *bps_collide = best[2];
+    return LBPM_OK;
+}
+
+lbpm_status lbpm_batch_launch_count(const lbpm_batch* b, long long* launches) {
+    if (!b || !launches) return LBPM_E_INVALID;
+    *launches = b->launches;
+    return LBPM_OK;
+}
+
+}  // extern "C"

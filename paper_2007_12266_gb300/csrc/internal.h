@@ -117,6 +117,20 @@ cudaError_t launch_collide(const lbpm_ctx* c, int parity, cudaStream_t s);
 cudaError_t launch_reservoir(const lbpm_ctx* c, int parity, cudaStream_t s);
 
 constexpr int NSUM = 27;  // per-site sums reduced by the measure kernel
+void fill_measures(const lbpm_ctx* c, const double* S, lbpm_measures* out);
+
+// One tile of a batched launch: `first` is the first thread index (site, or
+// site/halo entry for the phase pass) of job `job` that the block handles.
+struct BatchTile {
+    int job;
+    int first;
+};
+cudaError_t launch_batch(int kernel, int par, bool fp16, int bt, unsigned grid, cudaStream_t s,
+                         const DomainView* v, const BatchTile* t, int nt);
+cudaError_t launch_batch_measure(bool fp16, unsigned grid, cudaStream_t s, const DomainView* v, const int* parity,
+                                 const BatchTile* t, int nt, double* partials, const int* tile_begin, int n_jobs,
+                                 double* out);
+int batch_max_blocks(int kernel, bool fp16, int bt);
 cudaError_t launch_measure(lbpm_ctx* c, int parity, double* d_out, cudaStream_t s);
 cudaError_t launch_field(const lbpm_ctx* c, int parity, int which, float* dense, cudaStream_t s);
 cudaError_t launch_export_dist(const lbpm_ctx* c, int parity, int which, float* out, cudaStream_t s);

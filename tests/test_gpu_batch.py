@@ -1,0 +1,109 @@
+"""Batched form: several jobs in one persistent launch per phase (GPU only).
+
+Each site is computed by the same device code with the same arithmetic
+whether its domain runs alone or inside a batch, so batched results must be
+bit-identical to running every job alone; the batched fp64 measures sum in
+another order and agree to round-off.
+"""
+import numpy as np
+import pytest
+
+from synthetic import phi0_blob, phi0_iid, random_affinity, sphere_pack, uniform_affinity
+
+pytestmark = pytest.mark.gpu
+
+
+def _jobs():
+    """Uneven jobs: sizes, periodicities, wetting, tau, force and a reservoir job."""
+    specs = []
+    for j, (L, por, per, kw) in enumerate([
+            ((24, 20, 28), 0.35, (1, 1, 1), dict(tau_a=0.7, tau_b=0.7, force=(0, 0, 1e-5))),
+            ((16, 16, 16), 0.45, (0, 0, 1), dict(tau_a=0.9, tau_b=0.6, force=(0, 1e-5, 2e-5))),
+            ((40, 12, 20), 0.30, (1, 0, 1), dict(tau_a=0.8, tau_b=0.8, force=(3e-5, 0, 0))),
+            ((12, 14, 30), 0.50, (1, 1, 0), dict(tau_a=0.7, tau_b=0.7, force=(0, 0, 2e-5),
+                                                 reservoir_z=1, rho_in=1.001, rho_out=0.999))]):
+        sp = sphere_pack(L, por, 2.5, 0.8, 40 + j)
+        lab = sp.labels
+        aff = random_affinity(lab, -0.8, 0.8, 60 + j)
+        phi0 = phi0_blob(lab, 0.45, 70 + j, sigma=2.0) if j % 2 else phi0_iid(lab, 0.5, 80 + j)
+        kw = dict(kw, alpha=0.005, beta=0.95)
+        specs.append((lab, aff, phi0, per, kw))
+    return specs
+
+
+def _make(spec, precision):
+    import paper_2007_12266_gb300 as lbm
+    lab, aff, phi0, per, kw = spec
+    d = lbm.Domain(lab, aff, periodic=per, precision=precision, **kw)
+    d.init_fluids(phi0)
+    return d
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp16"])
+def test_batch_bit_identical_to_alone(precision):
+    import paper_2007_12266_gb300 as lbm
+    specs = _jobs()
+    alone = [_make(s, precision) for s in specs]
+    batched = [_make(s, precision) for s in specs]
+    b = lbm.Batch()
+    for d in batched:
+        b.add(d)
+    b.advance(10)
+    b.advance(14)
+    for d in alone:
+        d.advance(24)
+    for da, db in zip(alone, batched):
+        assert db.step_count == 24
+        for which in ("f", "a", "b"):
+            assert np.array_equal(da.distributions(which), db.distributions(which)), which
+    # measures: batched fp64 reduction vs per-job reduction
+    mb = b.measure()
+    for d, m in zip(alone, mb):
+        mo = d.measure()
+        for k in ("sat_mass", "mass_a", "mass_b", "mass_total", "vol_a", "p_a", "p_b", "ca"):
+            assert abs(m[k] - mo[k]) <= 1e-12 * max(abs(mo[k]), 1e-30), k
+        for k in ("flux", "mom_a", "mom_b"):
+            assert np.allclose(m[k], mo[k], rtol=1e-9, atol=1e-18), k
+    b.close()
+
+
+def test_batch_membership_and_tuner():
+    import paper_2007_12266_gb300 as lbm
+    specs = _jobs()[:3]
+    alone = [_make(s, "fp32") for s in specs]
+    batched = [_make(s, "fp32") for s in specs]
+    b = lbm.Batch()
+    for d in batched[:2]:
+        b.add(d)
+    b.advance(6)
+    b.add(batched[2])              # joins at step 0 while the others are at 6
+    threads, p, c = b.tune(steps_per_candidate=2)
+    assert threads in (128, 256, 512) and p >= 1 and c >= 1
+    b.remove(batched[0])
+    b.advance(4)
+    batched[0].advance(8)          # continues alone
+    steps = [d.step_count for d in batched]
+    for d, n in zip(alone, steps):
+        d.advance(n)
+    for da, db in zip(alone, batched):
+        assert np.array_equal(da.distributions("f"), db.distributions("f"))
+        assert np.array_equal(da.distributions("b"), db.distributions("b"))
+    b.close()
+
+
+def test_batch_rejects_bad_jobs():
+    import paper_2007_12266_gb300 as lbm
+    specs = _jobs()
+    b = lbm.Batch()
+    d32 = _make(specs[0], "fp32")
+    d16 = _make(specs[1], "fp16")
+    b.add(d32)
+    with pytest.raises(lbm.LBPMError):
+        b.add(d16)                 # another precision
+    odd = _make(specs[2], "fp32")
+    odd.advance(1)
+    with pytest.raises(lbm.LBPMError):
+        b.add(odd)                 # odd step
+    with pytest.raises(lbm.LBPMError):
+        b.advance(3)               # bundles are even
+    b.close()
