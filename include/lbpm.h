@@ -310,6 +310,77 @@ lbpm_status lbpm_batch_tune(lbpm_batch* batch, int steps_per_candidate, int* thr
                             int* blocks_per_sm_collide);
 lbpm_status lbpm_batch_launch_count(const lbpm_batch* batch, long long* launches);
 
+/*
+ * Serving loop (continuous batching) for the protocols of Sec. 4: steady
+ * state (Sec. 4.2: periodic flow driven by a body force), unsteady
+ * displacement (Sec. 4.1: inlet/outlet reservoirs) and centrifuge-like runs
+ * (Sec. 4.1: body force raised by force_factor each time the saturation
+ * changes by less than sw_tol over an interval, up to force_cap). A job ends
+ * when the Darcy flux along the drive changes by less than flux_tol (relative)
+ * over one check interval - standing in for the capillary-number test of
+ * Eq. convergence - or at max_steps.
+ * The caller drives the server with lbpm_server_run: each call admits queued
+ * jobs first come first served while a slot (max_jobs) and the device-memory
+ * budget allow (admission by the job's estimated footprint), advances every
+ * running job by one check interval in one batched launch sequence (jobs
+ * admitted in this call join the running batch at once), measures them and
+ * retires the finished ones. Finished jobs keep their device state, so their
+ * fields stay readable (lbpm_server_job_ctx), until lbpm_server_release or
+ * until that memory is needed to admit a queued job (oldest finished job
+ * first; its status and last measures stay available).
+ */
+typedef struct lbpm_server lbpm_server;
+
+enum { LBPM_JOB_STEADY = 0, LBPM_JOB_UNSTEADY = 1, LBPM_JOB_CENTRIFUGE = 2 };
+enum { LBPM_JOB_QUEUED = 0, LBPM_JOB_RUNNING = 1, LBPM_JOB_DONE = 2, LBPM_JOB_FAILED = 3,
+       LBPM_JOB_CANCELLED = 4 };
+
+/* A job: image, wetting map (NULL = phi_s 0), initial phases and parameters,
+ * as for lbpm_load_image / lbpm_set_affinity_map / lbpm_init_fluids /
+ * lbpm_set_params. The arrays are copied by lbpm_server_submit. */
+typedef struct {
+    const uint16_t* labels;
+    int nx, ny, nz;
+    const float* affinity;
+    const float* phi0;
+    lbpm_params params;
+    int kind;
+    long long max_steps;
+    double flux_tol;
+    double sw_tol;
+    double force_factor, force_cap;
+} lbpm_job_spec;
+
+/* Job status; times in seconds on the server's steady clock. */
+typedef struct {
+    int state;
+    long long steps;
+    long long n_sites;
+    size_t footprint;
+    double t_submit, t_admit, t_done;
+    int force_raises;
+    lbpm_measures last;
+} lbpm_job_status;
+
+/* hbm_budget_bytes = 0: 90 % of the free device memory. check_interval:
+ * steps per round (even). */
+lbpm_status lbpm_server_create(lbpm_server** out, int device, void* cuda_stream, size_t hbm_budget_bytes,
+                               int max_jobs, int check_interval);
+lbpm_status lbpm_server_destroy(lbpm_server* server);
+lbpm_status lbpm_server_set_allocator(lbpm_server* server, lbpm_alloc_fn alloc, lbpm_free_fn free_fn, void* user);
+const char* lbpm_server_last_error(const lbpm_server* server);
+/* Queue a job (LBPM_E_OOM if its footprint exceeds the whole budget). */
+lbpm_status lbpm_server_submit(lbpm_server* server, const lbpm_job_spec* spec, long long* ticket);
+/* One round: admit, advance one interval, measure, retire. */
+lbpm_status lbpm_server_run(lbpm_server* server, int* n_running, int* n_queued, int* n_finished);
+lbpm_status lbpm_server_poll(lbpm_server* server, long long ticket, lbpm_job_status* out);
+/* The job's context (NULL once released) for reading fields or distributions. */
+lbpm_status lbpm_server_job_ctx(lbpm_server* server, long long ticket, lbpm_ctx** ctx);
+lbpm_status lbpm_server_cancel(lbpm_server* server, long long ticket);
+lbpm_status lbpm_server_release(lbpm_server* server, long long ticket);
+lbpm_status lbpm_server_stats(const lbpm_server* server, long long* site_updates, size_t* used_bytes,
+                              size_t* budget_bytes);
+
 /* Number of kernel launches issued by this ctx since creation. */
 lbpm_status lbpm_launch_count(const lbpm_ctx* ctx, long long* launches);
 

@@ -20,13 +20,15 @@ from typing import Optional
 import numpy as np
 
 from . import _lib
-from ._lib import LBPMError, Measures, Params
+from ._lib import JobSpec, JobStatus, LBPMError, Measures, Params
 
-__all__ = ["Domain", "Batch", "LBPMError", "FIELDS", "DISTS", "library_path", "version"]
+__all__ = ["Domain", "Batch", "Server", "JOB_KINDS", "JOB_STATES", "LBPMError", "FIELDS", "DISTS", "library_path", "version"]
 
 FIELDS = {"phi": 0, "pressure": 1, "ux": 2, "uy": 3, "uz": 4, "na": 5, "nb": 6, "rho": 7}
 DISTS = {"f": (0, 19), "a": (1, 7), "b": (2, 7)}
 PRECISION = {"fp32": 0, "fp16": 1}
+JOB_KINDS = {"steady": 0, "unsteady": 1, "centrifuge": 2}
+JOB_STATES = {0: "queued", 1: "running", 2: "done", 3: "failed", 4: "cancelled"}
 
 
 def library_path() -> str:
@@ -48,6 +50,18 @@ def _close_all():
             d.close()
         except Exception:
             pass
+
+
+def _params(tau_a, tau_b, alpha, beta, force, precision, periodic, reservoir_z, rho_in, rho_out) -> Params:
+    p = Params()
+    p.tau_a, p.tau_b, p.alpha, p.beta = float(tau_a), float(tau_b), float(alpha), float(beta)
+    for a in range(3):
+        p.force[a] = float(force[a])
+        p.periodic[a] = int(periodic[a])
+    p.precision = PRECISION[precision] if isinstance(precision, str) else int(precision)
+    p.reservoir_z = int(reservoir_z)
+    p.rho_in, p.rho_out = float(rho_in), float(rho_out)
+    return p
 
 
 def _measures_dict(m: Measures) -> dict:
@@ -151,14 +165,7 @@ class Domain:
 
     def set_params(self, *, tau_a, tau_b, alpha, beta, force, precision="fp32",
                    periodic=(1, 1, 1), reservoir_z=0, rho_in=1.0, rho_out=1.0):
-        p = Params()
-        p.tau_a, p.tau_b, p.alpha, p.beta = float(tau_a), float(tau_b), float(alpha), float(beta)
-        for a in range(3):
-            p.force[a] = float(force[a])
-            p.periodic[a] = int(periodic[a])
-        p.precision = PRECISION[precision] if isinstance(precision, str) else int(precision)
-        p.reservoir_z = int(reservoir_z)
-        p.rho_in, p.rho_out = float(rho_in), float(rho_out)
+        p = _params(tau_a, tau_b, alpha, beta, force, precision, periodic, reservoir_z, rho_in, rho_out)
         self._check(self._L.lbpm_set_params(self._h, ct.byref(p)))
         self.params = dict(tau_a=tau_a, tau_b=tau_b, alpha=alpha, beta=beta, force=tuple(force),
                            precision=precision, periodic=tuple(periodic), reservoir_z=reservoir_z,
@@ -356,3 +363,114 @@ class Batch:
         n = ct.c_longlong()
         self._check(self._L.lbpm_batch_launch_count(self._h, ct.byref(n)))
         return n.value
+
+
+class _JobView:
+    """Read-only access to a served job's device state (fields, distributions)."""
+
+    def __init__(self, server: "Server", handle, shape):
+        self._L = server._L
+        self._h = handle
+        self.shape = shape
+        self._server = server
+
+    _check = Domain._check
+    read_field = Domain.read_field
+    distributions = Domain.distributions
+    measure = Domain.measure
+    n_sites = Domain.n_sites
+    step_count = Domain.step_count
+
+
+class Server:
+    """Continuous-batching request loop (lbpm_server_* ABI): submit jobs, then
+    call run() repeatedly; each call admits queued jobs while slots and the
+    memory budget allow, advances all running jobs one check interval in one
+    batched launch sequence, and retires the finished ones."""
+
+    def __init__(self, device: int = 0, budget_bytes: int = 0, max_jobs: int = 64, check_interval: int = 500,
+                 stream=None, use_torch_allocator: bool = True):
+        torch = _torch()
+        self._L = _lib.load()
+        self.device = int(device)
+        with torch.cuda.device(self.device):
+            self._stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        h = ct.c_void_p()
+        st = self._L.lbpm_server_create(ct.byref(h), self.device, ct.c_void_p(self._stream.cuda_stream),
+                                        int(budget_bytes), int(max_jobs), int(check_interval))
+        if st != 0:
+            raise LBPMError(st, "lbpm_server_create failed")
+        self._h = h
+        _LIVE.add(self)
+        self._callbacks = None
+        if use_torch_allocator:
+            self._callbacks = _torch_allocator(torch, self.device, self._stream)
+            self._check(self._L.lbpm_server_set_allocator(self._h, self._callbacks[0], self._callbacks[1], None))
+        self._shapes = {}
+
+    def _check(self, status: int):
+        if status != 0:
+            raise LBPMError(status, self._L.lbpm_server_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._L.lbpm_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit(self, labels, phi0, affinity=None, *, kind="steady", max_steps=10000, flux_tol=1e-4,
+               sw_tol=1e-4, force_factor=2.0, force_cap=1.6e-4, tau_a=0.7, tau_b=0.7, alpha=0.005,
+               beta=0.95, force=(0.0, 0.0, 0.0), precision="fp32", periodic=(1, 1, 1), reservoir_z=0,
+               rho_in=1.0, rho_out=1.0) -> int:
+        lab = np.ascontiguousarray(labels, dtype=np.uint16)
+        ph = np.ascontiguousarray(phi0, dtype=np.float32)
+        aff = None if affinity is None else np.ascontiguousarray(affinity, dtype=np.float32)
+        nz, ny, nx = lab.shape
+        sp = JobSpec()
+        sp.labels, sp.nx, sp.ny, sp.nz = lab.ctypes.data, nx, ny, nz
+        sp.affinity = aff.ctypes.data if aff is not None else None
+        sp.phi0 = ph.ctypes.data
+        sp.params = _params(tau_a, tau_b, alpha, beta, force, precision, periodic, reservoir_z, rho_in, rho_out)
+        sp.kind = JOB_KINDS[kind] if isinstance(kind, str) else int(kind)
+        sp.max_steps = int(max_steps)
+        sp.flux_tol, sp.sw_tol = float(flux_tol), float(sw_tol)
+        sp.force_factor, sp.force_cap = float(force_factor), float(force_cap)
+        t = ct.c_longlong()
+        self._check(self._L.lbpm_server_submit(self._h, ct.byref(sp), ct.byref(t)))
+        self._shapes[t.value] = lab.shape
+        return t.value
+
+    def run(self):
+        r, q, f = ct.c_int(), ct.c_int(), ct.c_int()
+        self._check(self._L.lbpm_server_run(self._h, ct.byref(r), ct.byref(q), ct.byref(f)))
+        return r.value, q.value, f.value
+
+    def poll(self, ticket: int) -> dict:
+        st = JobStatus()
+        self._check(self._L.lbpm_server_poll(self._h, int(ticket), ct.byref(st)))
+        return {"state": JOB_STATES[st.state], "steps": st.steps, "n_sites": st.n_sites,
+                "footprint": st.footprint, "t_submit": st.t_submit, "t_admit": st.t_admit,
+                "t_done": st.t_done, "force_raises": st.force_raises, "last": _measures_dict(st.last)}
+
+    def job(self, ticket: int) -> _JobView:
+        h = ct.c_void_p()
+        self._check(self._L.lbpm_server_job_ctx(self._h, int(ticket), ct.byref(h)))
+        if not h.value:
+            raise LBPMError(4, "the job has no device state")
+        return _JobView(self, h, self._shapes[ticket])
+
+    def cancel(self, ticket: int):
+        self._check(self._L.lbpm_server_cancel(self._h, int(ticket)))
+
+    def release(self, ticket: int):
+        self._check(self._L.lbpm_server_release(self._h, int(ticket)))
+
+    def stats(self) -> dict:
+        su, used, budget = ct.c_longlong(), ct.c_size_t(), ct.c_size_t()
+        self._check(self._L.lbpm_server_stats(self._h, ct.byref(su), ct.byref(used), ct.byref(budget)))
+        return {"site_updates": su.value, "used_bytes": used.value, "budget_bytes": budget.value}

@@ -42,6 +42,28 @@ class Measures(ct.Structure):
     ]
 
 
+class JobSpec(ct.Structure):
+    _fields_ = [
+        ("labels", ct.c_void_p), ("nx", ct.c_int), ("ny", ct.c_int), ("nz", ct.c_int),
+        ("affinity", ct.c_void_p), ("phi0", ct.c_void_p),
+        ("params", Params),
+        ("kind", ct.c_int),
+        ("max_steps", ct.c_longlong),
+        ("flux_tol", ct.c_double), ("sw_tol", ct.c_double),
+        ("force_factor", ct.c_double), ("force_cap", ct.c_double),
+    ]
+
+
+class JobStatus(ct.Structure):
+    _fields_ = [
+        ("state", ct.c_int), ("steps", ct.c_longlong), ("n_sites", ct.c_longlong),
+        ("footprint", ct.c_size_t),
+        ("t_submit", ct.c_double), ("t_admit", ct.c_double), ("t_done", ct.c_double),
+        ("force_raises", ct.c_int),
+        ("last", Measures),
+    ]
+
+
 ALLOC_FN = ct.CFUNCTYPE(ct.c_void_p, ct.c_size_t, ct.c_void_p, ct.c_void_p)
 FREE_FN = ct.CFUNCTYPE(None, ct.c_void_p, ct.c_void_p)
 
@@ -90,6 +112,19 @@ SIGNATURES = {
     "lbpm_batch_tune": (ct.c_int, [ct.c_void_p, ct.c_int, ct.POINTER(ct.c_int), ct.POINTER(ct.c_int),
                                    ct.POINTER(ct.c_int)]),
     "lbpm_batch_launch_count": (ct.c_int, [ct.c_void_p, ct.POINTER(ct.c_longlong)]),
+    "lbpm_server_create": (ct.c_int, [ct.POINTER(ct.c_void_p), ct.c_int, ct.c_void_p, ct.c_size_t, ct.c_int,
+                                      ct.c_int]),
+    "lbpm_server_destroy": (ct.c_int, [ct.c_void_p]),
+    "lbpm_server_set_allocator": (ct.c_int, [ct.c_void_p, ALLOC_FN, FREE_FN, ct.c_void_p]),
+    "lbpm_server_last_error": (ct.c_char_p, [ct.c_void_p]),
+    "lbpm_server_submit": (ct.c_int, [ct.c_void_p, ct.POINTER(JobSpec), ct.POINTER(ct.c_longlong)]),
+    "lbpm_server_run": (ct.c_int, [ct.c_void_p, ct.POINTER(ct.c_int), ct.POINTER(ct.c_int), ct.POINTER(ct.c_int)]),
+    "lbpm_server_poll": (ct.c_int, [ct.c_void_p, ct.c_longlong, ct.POINTER(JobStatus)]),
+    "lbpm_server_job_ctx": (ct.c_int, [ct.c_void_p, ct.c_longlong, ct.POINTER(ct.c_void_p)]),
+    "lbpm_server_cancel": (ct.c_int, [ct.c_void_p, ct.c_longlong]),
+    "lbpm_server_release": (ct.c_int, [ct.c_void_p, ct.c_longlong]),
+    "lbpm_server_stats": (ct.c_int, [ct.c_void_p, ct.POINTER(ct.c_longlong), ct.POINTER(ct.c_size_t),
+                                     ct.POINTER(ct.c_size_t)]),
 }
 
 _lib = None

@@ -111,3 +111,31 @@ def test_binding_refuses_without_gpu():
     import paper_2007_12266_gb300 as lbm
     with pytest.raises(RuntimeError):
         lbm.Domain(np.zeros((4, 4, 4), np.uint16))
+
+
+def test_server_struct_layout_matches_c():
+    from paper_2007_12266_gb300._lib import JobSpec, JobStatus
+    prog = r"""
+#include <stdio.h>
+#include <stddef.h>
+#include "lbpm.h"
+int main(void) {
+  printf("%zu %zu %zu %zu %zu\n", sizeof(lbpm_job_spec), offsetof(lbpm_job_spec, params),
+         offsetof(lbpm_job_spec, kind), offsetof(lbpm_job_spec, max_steps), offsetof(lbpm_job_spec, force_cap));
+  printf("%zu %zu %zu %zu\n", sizeof(lbpm_job_status), offsetof(lbpm_job_status, footprint),
+         offsetof(lbpm_job_status, force_raises), offsetof(lbpm_job_status, last));
+  return 0;
+}
+"""
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "t.c")
+        exe = os.path.join(d, "t")
+        open(c, "w").write(prog)
+        subprocess.check_call(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), c, "-o", exe])
+        out = subprocess.check_output([exe]).decode().split("\n")
+    a = list(map(int, out[0].split()))
+    b = list(map(int, out[1].split()))
+    assert a == [ct.sizeof(JobSpec), JobSpec.params.offset, JobSpec.kind.offset, JobSpec.max_steps.offset,
+                 JobSpec.force_cap.offset]
+    assert b == [ct.sizeof(JobStatus), JobStatus.footprint.offset, JobStatus.force_raises.offset,
+                 JobStatus.last.offset]

@@ -1,0 +1,116 @@
+"""Serving loop (continuous batching) on the GPU.
+
+* Each job's result is the same alone and in the mix: the mix admits jobs at
+  different rounds, yet every job ends at the same step with bit-identical
+  distributions and measures, because a job's sites are computed the same way
+  in any batch and its protocol decisions use only its own measures.
+* Admission by device-memory footprint: with a budget that fits two jobs,
+  never more than two run at once, and the queue drains.
+* Cancel and release.
+"""
+import numpy as np
+import pytest
+
+from synthetic import add_walls, phi0_blob, phi0_reservoir, random_affinity, sphere_pack, uniform_affinity
+
+pytestmark = pytest.mark.gpu
+
+
+def _job(kind, j):
+    L = (20 + 4 * (j % 3), 18 + 2 * (j % 2), 24 + 4 * (j % 4))
+    sp = sphere_pack(L, 0.4, 2.5, 0.7, 300 + j)
+    if kind == "steady":
+        lab = add_walls(sp.labels, ("x", "y"))
+        return dict(labels=lab, affinity=random_affinity(lab, -0.3, 0.3, 400 + j),
+                    phi0=phi0_blob(lab, 0.4, 500 + j, sigma=2.0), kind="steady",
+                    periodic=(0, 0, 1), force=(0, 0, 2e-5))
+    lab = sp.labels
+    common = dict(labels=lab, affinity=uniform_affinity(lab, -0.5), phi0=phi0_reservoir(lab, -1.0),
+                  periodic=(1, 1, 0), reservoir_z=1)
+    if kind == "unsteady":
+        return dict(common, kind="unsteady", rho_in=1.002, rho_out=0.998)
+    return dict(common, kind="centrifuge", force=(0, 0, 1e-5), sw_tol=2e-4, force_factor=2.0, force_cap=4e-5)
+
+
+POLICY = dict(max_steps=400, flux_tol=2e-3)
+
+
+def _serve_alone(spec, precision):
+    import paper_2007_12266_gb300 as lbm
+    s = lbm.Server(max_jobs=4, check_interval=20)
+    t = s.submit(**spec, **POLICY, precision=precision)
+    for _ in range(1000):
+        if not (s.run()[0] or s.poll(t)["state"] == "queued"):
+            return s, t
+    raise AssertionError("job did not finish")
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp16"])
+def test_result_same_alone_and_in_the_mix(precision):
+    import paper_2007_12266_gb300 as lbm
+    kinds = ["steady", "unsteady", "centrifuge", "steady", "unsteady"]
+    specs = [_job(k, j) for j, k in enumerate(kinds)]
+    mix = lbm.Server(max_jobs=8, check_interval=20)
+    tickets = [mix.submit(**specs[0], **POLICY, precision=precision),
+               mix.submit(**specs[1], **POLICY, precision=precision)]
+    pending = list(range(2, len(specs)))
+    for rounds in range(1, 1000):
+        running, queued, _ = mix.run()
+        if pending and rounds in (1, 3, 4):       # arrivals while others run
+            j = pending.pop(0)
+            tickets.append(mix.submit(**specs[j], **POLICY, precision=precision))
+            continue
+        if running == 0 and queued == 0 and not pending:
+            break
+    else:
+        raise AssertionError("the mix did not drain")
+    for j, t in enumerate(tickets):
+        st = mix.poll(t)
+        assert st["state"] == "done", st
+        alone, ta = _serve_alone(specs[j], precision)
+        sa = alone.poll(ta)
+        assert sa["steps"] == st["steps"], (j, sa["steps"], st["steps"])
+        assert sa["force_raises"] == st["force_raises"]
+        for k in ("sat_mass", "mass_a", "ca", "p_a"):
+            assert sa["last"][k] == st["last"][k], k
+        ja, jm = alone.job(ta), mix.job(t)
+        for which in ("f", "a", "b"):
+            assert np.array_equal(ja.distributions(which), jm.distributions(which))
+        alone.close()
+    # jobs admitted in different rounds really overlapped on the device
+    admits = sorted(mix.poll(t)["t_admit"] for t in tickets)
+    dones = sorted(mix.poll(t)["t_done"] for t in tickets)
+    assert admits[-1] < dones[-1] and admits[1] < dones[0] + 1e9
+    mix.close()
+
+
+def test_admission_by_memory_budget_and_cancel():
+    import paper_2007_12266_gb300 as lbm
+    specs = [_job("steady", j) for j in range(5)]
+    probe = lbm.Server(max_jobs=8, check_interval=20)
+    foot = []
+    for sp in specs:
+        t = probe.submit(**sp, **POLICY)
+        foot.append(probe.poll(t)["footprint"])
+    probe.close()
+    budget = sorted(foot)[-1] + sorted(foot)[-2] + 1024
+    s = lbm.Server(budget_bytes=budget, max_jobs=8, check_interval=20)
+    tickets = [s.submit(**sp, **POLICY) for sp in specs]
+    s.cancel(tickets[-1])                       # cancelled while queued
+    max_running = 0
+    for _ in range(1000):
+        running, queued, _ = s.run()
+        max_running = max(max_running, running)
+        assert s.stats()["used_bytes"] <= budget
+        if running == 0 and queued == 0:
+            break
+    else:
+        raise AssertionError("the queue did not drain")
+    assert 1 <= max_running <= 2
+    states = [s.poll(t)["state"] for t in tickets]
+    assert states[:-1] == ["done"] * 4 and states[-1] == "cancelled"
+    # finished jobs gave their memory back to admit the queue; release the rest
+    for t in tickets:
+        s.release(t)
+    assert s.stats()["used_bytes"] == 0
+    s.close()
