@@ -187,6 +187,110 @@ def bench_reference(args):
     return 0
 
 
+def _spawn_map(fn, items):
+    """Generate synthetic inputs in parallel (spawned interpreters, no CUDA)."""
+    import multiprocessing as mp
+    n = max(1, min(len(items), os.cpu_count() or 1, 16))
+    if n == 1:
+        return [fn(i) for i in items]
+    with mp.get_context("spawn").Pool(n) as pool:
+        return pool.map(fn, items, chunksize=1)
+
+
+def _batched_job(j):
+    from synthetic import workload_batched_job
+    return workload_batched_job(j)
+
+
+def _serving_job(args):
+    from synthetic import serving_job
+    i, choices = args
+    return serving_job(i, L_choices=choices)
+
+
+def _domain(lbm, w, precision, device):
+    d = lbm.Domain(w.labels, w.affinity, periodic=w.periodic, tau_a=w.tau_a, tau_b=w.tau_b, alpha=w.alpha,
+                   beta=w.beta, force=w.force, precision=precision, reservoir_z=w.reservoir_z,
+                   rho_in=w.rho_in, rho_out=w.rho_out, device=device)
+    d.init_fluids(w.phi0)
+    return d
+
+
+def bench_batched(jobs, precision, steps, device):
+    """Batched form: all jobs in one persistent launch per phase, tuned shape."""
+    import torch
+
+    import paper_2007_12266_gb300 as lbm
+    doms = [_domain(lbm, w, precision, device) for w in jobs]
+    b = lbm.Batch(device=device)
+    for d in doms:
+        b.add(d)
+    shape = b.tune(steps_per_candidate=4)
+    b.advance(20)
+    stream = torch.cuda.current_stream(device)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(device)
+    l0 = b.launch_count
+    e0.record(stream)
+    b.advance(steps)
+    e1.record(stream)
+    torch.cuda.synchronize(device)
+    ms = e0.elapsed_time(e1)
+    meas = b.measure()
+    n = b.n_sites
+    out = {"value": n * steps / (ms * 1e-3) / 1e6, "unit": "MLUPS", "n_jobs": len(jobs), "n_sites": n,
+           "steps": steps, "ms": ms, "launch_shape": {"threads": shape[0], "blocks_per_sm_phase": shape[1],
+                                                      "blocks_per_sm_collide": shape[2]},
+           "gpu_launches": b.launch_count - l0, "unstable_jobs": sum(1 for m in meas if m["status"])}
+    b.close()
+    for d in doms:
+        d.close()
+    return out
+
+
+def bench_serving(jobs, precision, lam, seed, max_steps, interval, device, flux_tol=1e-4):
+    """Continuous-batching server fed by a seeded Poisson arrival stream."""
+    import numpy as np
+
+    import paper_2007_12266_gb300 as lbm
+    rng = np.random.default_rng(seed)
+    arrivals = np.cumsum(rng.exponential(1.0 / lam, size=len(jobs)))
+    srv = lbm.Server(device=device, max_jobs=len(jobs), check_interval=interval)
+    tickets = []
+    t0 = time.perf_counter()
+    nxt = 0
+    rounds = 0
+    for rounds in range(1, 1_000_000):
+        now = time.perf_counter() - t0
+        while nxt < len(jobs) and arrivals[nxt] <= now:
+            w = jobs[nxt]
+            kind = w.meta["kind"]
+            tickets.append(srv.submit(w.labels, w.phi0, w.affinity, kind=kind, max_steps=max_steps,
+                                      flux_tol=flux_tol, sw_tol=1e-4, force_factor=2.0, force_cap=1.6e-4,
+                                      tau_a=w.tau_a, tau_b=w.tau_b, alpha=w.alpha, beta=w.beta, force=w.force,
+                                      precision=precision, periodic=w.periodic, reservoir_z=w.reservoir_z))
+            nxt += 1
+        running, queued, _ = srv.run()
+        if running == 0 and queued == 0:
+            if nxt == len(jobs):
+                break
+            time.sleep(max(0.0, arrivals[nxt] - (time.perf_counter() - t0)))
+    wall = time.perf_counter() - t0
+    st = [srv.poll(t) for t in tickets]
+    lat = np.array([s["t_done"] - s["t_submit"] for s in st])
+    run_t = np.array([s["t_done"] - s["t_admit"] for s in st])
+    su = srv.stats()["site_updates"]
+    out = {"p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
+           "p50_run_s": float(np.percentile(run_t, 50)), "aggregate_value": su / wall / 1e6,
+           "unit": "MLUPS", "n_jobs": len(jobs), "wall_s": wall, "rounds": rounds,
+           "arrival_rate_per_s": lam, "check_interval": interval, "max_steps": max_steps,
+           "states": {k: sum(1 for s in st if s["state"] == k) for k in ("done", "failed")},
+           "converged_early": sum(1 for s in st if s["steps"] < max_steps),
+           "kinds": {k: sum(1 for w in jobs if w.meta["kind"] == k) for k in ("steady", "unsteady", "centrifuge")}}
+    srv.close()
+    return out
+
+
 def bench_gpu(args):
     import numpy as np
     import torch
@@ -273,6 +377,61 @@ def bench_gpu(args):
     h2d = w.labels.nbytes + w.affinity.nbytes + w.phi0.nbytes
     e2e_dom.close()
 
+    # the same workload with FP16 storage
+    fp16 = None
+    if prec == "fp32" and not args.no_fp16:
+        d16 = lbm.Domain(w.labels, w.affinity, device=local_rank, **dict(kw, precision="fp16"))
+        d16.init_fluids(w.phi0)
+        for _ in range(args.warmup):
+            d16.advance(bundle)
+            d16.measure()
+        torch.cuda.synchronize(dev)
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(args.steps):
+            d16.advance(bundle)
+            m16 = d16.measure()
+        f1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms16 = f0.elapsed_time(f1)
+        d16.enable_kernel_timing(True)
+        d16.kernel_timing()
+        d16.advance(bundle * 2)
+        kt16 = d16.kernel_timing()
+        d16.close()
+        v16 = N * bundle * args.steps / (ms16 * 1e-3) / 1e6
+        fp16 = {"value": v16, "unit": "MLUPS", "ms_per_step": ms16 / args.steps, "ratio_vs_fp32": v16 / value,
+                "step_achieved_gbs": BYTES_STEP_FP16 * N * bundle * args.steps / (ms16 * 1e-3) / 1e9,
+                "collide_avg_launch_ms": kt16["collide_ms"] / max(kt16["collide_launches"], 1),
+                "phase_avg_launch_ms": kt16["phase_ms"] / max(kt16["phase_launches"], 1),
+                "sat_mass": m16["sat_mass"], "flux_z": m16["flux"][2]}
+
+    batched = None
+    if not args.no_batched and world == 1:
+        try:
+            jobs = _spawn_map(_batched_job, list(range(args.batched_jobs)))
+            batched = {"workload": f"{len(jobs)} sphere-pack jobs, L in {{64..192}}, porosity U[0.15,0.35]",
+                       "fp32": bench_batched(jobs, "fp32", args.batched_steps, local_rank),
+                       "fp16": bench_batched(jobs, "fp16", args.batched_steps, local_rank)}
+            batched["fp16_vs_fp32"] = batched["fp16"]["value"] / batched["fp32"]["value"]
+            batched["fp16_vs_plain_fp32"] = batched["fp16"]["value"] / value
+            del jobs
+        except Exception as exc:
+            batched = {"error": repr(exc)}
+
+    serving = None
+    if not args.no_serving and world == 1:
+        try:
+            choices = (64, 96, 128, 160)
+            sj = _spawn_map(_serving_job, [(i, choices) for i in range(args.serving_jobs)])
+            serving = bench_serving(sj, "fp16", 20.0, 5, args.serving_max_steps, 500, local_rank)
+            serving["workload"] = (f"{len(sj)} Poisson arrivals at 20/s, L in {choices}, FP16 storage, "
+                                   f"flux-change 1e-4 every 500 steps or {args.serving_max_steps} steps")
+            serving["vs_plain_fp32"] = serving["aggregate_value"] / value
+            del sj
+        except Exception as exc:
+            serving = {"error": repr(exc)}
+
     peak, peak_kind = measured_peaks()
     bytes_c = BYTES_COLLIDE_FP32 if prec == "fp32" else BYTES_COLLIDE_FP16
     bytes_s = BYTES_STEP_FP32 if prec == "fp32" else BYTES_STEP_FP16
@@ -306,6 +465,9 @@ def bench_gpu(args):
                          "step_frac_of_8tbs": step_gbs / 8000.0},
             "e2e": {"value": e2e_value, "unit": "MLUPS", "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": 27 * 8, "steps": e2e_steps},
+            "fp16": fp16,
+            "batched": batched,
+            "serving": serving,
             "gpu_launches": int(launches),
             "clocks": clocks,
             "measures_last": {"sat_mass": m["sat_mass"], "flux_z": m["flux"][2], "ca": m["ca"],
@@ -342,6 +504,13 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16"])
     ap.add_argument("--cpu-steps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp16", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--batched-jobs", type=int, default=64)
+    ap.add_argument("--batched-steps", type=int, default=2000)
+    ap.add_argument("--serving-jobs", type=int, default=24)
+    ap.add_argument("--serving-max-steps", type=int, default=4000)
     args = ap.parse_args()
     if args.impl == "reference":
         return bench_reference(args)

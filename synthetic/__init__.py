@@ -21,5 +21,6 @@ from .spherepack import (  # noqa: F401
     workload_steady256,
     workload_precision1024,
     workload_batched_job,
+    serving_job,
     crop,
 )

@@ -235,3 +235,31 @@ def workload_batched_job(j: int) -> Workload:
         phi0=phi0_blob(lab, sw, 5000 + j), periodic=(0, 0, 1),
         force=(0.0, 0.0, fz), steps=2000,
         porosity=float(np.count_nonzero(lab == 0) / lab.size))
+
+
+def serving_job(i: int, seed: int = 5, L_choices=(64, 96, 128, 160, 192, 224, 256, 288, 320, 352, 384)) -> Workload:
+    """Job i of a serving trace: L uniform on L_choices, porosity U[0.15, 0.35],
+    r ~ LN(8, 2); kind mix 50 % steady state (x/y walls, z periodic, blob phi0,
+    F_z = 1e-5), 30 % unsteady displacement (reservoirs in z, interior phi0 = -1,
+    phi_s = -0.7, F_z = 1e-5) and 20 % centrifuge-like (reservoirs, F_z from 1e-5
+    doubled at each saturation plateau up to 1.6e-4)."""
+    rng = np.random.default_rng(seed * 100003 + i)
+    L = int(rng.choice(list(L_choices)))
+    por = float(rng.uniform(0.15, 0.35))
+    u = float(rng.uniform())
+    kind = "steady" if u < 0.5 else ("unsteady" if u < 0.8 else "centrifuge")
+    sp = sphere_pack(L, por, 8.0, 2.0, seed * 7919 + i)
+    if kind == "steady":
+        lab = add_walls(sp.labels, ("x", "y"))
+        w = Workload(name=f"serve{i}_steady_L{L}", labels=lab,
+                     affinity=random_affinity(lab, -0.3, 0.3, seed * 31 + i),
+                     phi0=phi0_blob(lab, float(rng.uniform(0.2, 0.8)), seed * 37 + i),
+                     periodic=(0, 0, 1), force=(0.0, 0.0, 1e-5), steps=10000)
+    else:
+        lab = sp.labels
+        w = Workload(name=f"serve{i}_{kind}_L{L}", labels=lab, affinity=uniform_affinity(lab, -0.7),
+                     phi0=phi0_reservoir(lab, -1.0), periodic=(1, 1, 0), force=(0.0, 0.0, 1e-5),
+                     reservoir_z=1, steps=10000)
+    w.meta = {"kind": kind, "L": L}
+    w.porosity = float(np.count_nonzero(lab == 0) / lab.size)
+    return w
