@@ -291,6 +291,98 @@ def bench_serving(jobs, precision, lam, seed, max_steps, interval, device, flux_
     return out
 
 
+def bench_precision(args):
+    """1024^3 displacement (reservoirs in z, phi_s = -0.7, F_z = 1e-5) in FP32 and
+    FP16 storage, plus per-quantity errors of both against the FP64 oracle on
+    the 128^3 crop [448, 576)^3 run as its own domain with the same boundaries."""
+    import numpy as np
+    import torch
+
+    import oracle
+    import paper_2007_12266_gb300 as lbm
+    from synthetic import crop, workload_precision1024
+    t0 = time.perf_counter()
+    w = workload_precision1024(args.size)
+    gen_s = time.perf_counter() - t0
+    kw = dict(tau_a=w.tau_a, tau_b=w.tau_b, alpha=w.alpha, beta=w.beta, force=w.force, periodic=w.periodic,
+              reservoir_z=1, rho_in=w.rho_in, rho_out=w.rho_out)
+    out = {"metric": "pore-site MLUPS, 1024^3 displacement, FP32 vs FP16 storage", "unit": "MLUPS",
+           "workload": f"{w.name}: porosity {w.porosity:.3f}, periodic x/y, reservoirs in z, phi_s -0.7",
+           "steps": args.precision_steps, "generation_s": gen_s}
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    for prec in ("fp32", "fp16"):
+        d = lbm.Domain(w.labels, w.affinity, precision=prec, **kw)
+        d.init_fluids(w.phi0)
+        N = d.n_sites
+        d.advance(20)
+        d.measure()
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        steps = 0
+        trace = []
+        while steps < args.precision_steps:
+            d.advance(500)
+            steps += 500
+            m = d.measure()
+            trace.append((steps + 20, m["sat_mass"], m["flux"][2]))
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1)
+        bps = BYTES_STEP_FP32 if prec == "fp32" else BYTES_STEP_FP16
+        peak, _ = measured_peaks()
+        gbs = bps * N * steps / (ms * 1e-3) / 1e9
+        out[prec] = {"value": N * steps / (ms * 1e-3) / 1e6, "n_sites": N, "ms_per_step": ms / steps,
+                     "step_achieved_gbs": gbs, "step_frac": gbs / peak, "trace": trace[-3:],
+                     "status": m["status"]}
+        d.close()
+        torch.cuda.empty_cache()
+    out["fp16_vs_fp32"] = out["fp16"]["value"] / out["fp32"]["value"]
+    # the 128^3 crop: oracle vs both storages
+    lo, hi = (448, 448, 448), (576, 576, 576)
+    if args.size < 1024:
+        c = args.size // 2
+        lo, hi = (c - 64, c - 64, c - 64), (c + 64, c + 64, c + 64)
+    lab, aff, phi0 = crop(w.labels, lo, hi), crop(w.affinity, lo, hi), crop(w.phi0, lo, hi)
+    del w
+    oracle.set_threads(os.cpu_count() or 1)
+    ref = oracle.Oracle(lab, aff, kw["periodic"], tau_a=kw["tau_a"], tau_b=kw["tau_b"], alpha=kw["alpha"],
+                        beta=kw["beta"], force=kw["force"], reservoir_z=1, rho_in=kw["rho_in"],
+                        rho_out=kw["rho_out"])
+    ref.init_fluids(phi0)
+    t1 = time.perf_counter()
+    ref.step(args.crop_steps)
+    oracle_s = time.perf_counter() - t1
+    mo = ref.measure()
+    phi_o, p_o, u_o = ref.fields()
+    sv, _ = ref.index()
+    crop_out = {"box": [lo, hi], "n_sites": ref.N, "steps": args.crop_steps, "oracle_s": oracle_s,
+                "oracle_threads": oracle.get_threads()}
+    keys = ("sat_mass", "mass_a", "mass_b", "mass_total", "p_a", "p_b", "ca", "sat_count")
+    for prec in ("fp32", "fp16"):
+        d = lbm.Domain(lab, aff, precision=prec, **kw)
+        d.init_fluids(phi0)
+        d.advance(args.crop_steps)
+        m = d.measure()
+        errs = {k: abs(m[k] - mo[k]) / max(abs(mo[k]), 1e-300) for k in keys}
+        for a, ax in enumerate("xyz"):
+            for f in ("flux", "flux_a", "flux_b"):
+                scale = max(abs(mo[f + "_z"]), 1e-300)
+                errs[f"{f}_{ax}"] = abs(m[f][a] - mo[f"{f}_{ax}"]) / scale
+        phi_g = d.read_field("phi").ravel()[sv]
+        uz_g = d.read_field("uz").ravel()[sv]
+        errs["phi_max_abs"] = float(np.abs(phi_g - phi_o).max())
+        errs["phi_rms"] = float(np.sqrt(np.mean((phi_g - phi_o) ** 2)))
+        errs["uz_rms_rel"] = float(np.sqrt(np.mean((uz_g - u_o[2]) ** 2)) / max(np.sqrt(np.mean(u_o[2] ** 2)), 1e-300))
+        crop_out[prec] = {k: float(v) for k, v in errs.items()}
+        d.close()
+    crop_out["oracle_measures"] = {k: mo[k] for k in ("sat_mass", "flux_z", "ca", "p_a", "p_b")}
+    out["crop"] = crop_out
+    print(json.dumps(out))
+    return 0
+
+
 def bench_gpu(args):
     import numpy as np
     import torch
@@ -499,6 +591,9 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--mode", default="headline", choices=["headline", "precision"])
+    ap.add_argument("--precision-steps", type=int, default=5000)
+    ap.add_argument("--crop-steps", type=int, default=5000)
     ap.add_argument("--size", type=int, default=256)
     ap.add_argument("--bundle", type=int, default=100)
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16"])
@@ -514,6 +609,8 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         return bench_reference(args)
+    if args.mode == "precision":
+        return bench_precision(args)
     return bench_gpu(args)
 
 

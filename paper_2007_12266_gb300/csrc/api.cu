@@ -64,6 +64,8 @@ void free_state(lbpm_ctx* c) {
     dfree(c, c->d_nsum);
     dfree(c, c->d_nab[0]);
     dfree(c, c->d_nab[1]);
+    dfree(c, c->d_drho);
+    c->d_drho = nullptr;
     c->d_f = c->d_a = c->d_b = nullptr;
     c->d_nsum = nullptr;
     c->d_nab[0] = c->d_nab[1] = nullptr;
@@ -102,7 +104,8 @@ lbpm_status alloc_state(lbpm_ctx* c) {
     if (c->params.precision == LBPM_FP16) {
         c->d_nab[0] = static_cast<float2*>(dalloc(c, sizeof(float2) * c->N));
         c->d_nab[1] = static_cast<float2*>(dalloc(c, sizeof(float2) * c->N));
-        ok = ok && c->d_nab[0] && c->d_nab[1];
+        c->d_drho = static_cast<float*>(dalloc(c, sizeof(float) * c->N));
+        ok = ok && c->d_nab[0] && c->d_nab[1] && c->d_drho;
     } else {
         c->d_nsum = static_cast<float*>(dalloc(c, sizeof(float) * c->N));
         ok = ok && c->d_nsum;

@@ -28,6 +28,8 @@ struct DomainView {
     float* nsum;           // [N] Na + Nb of the current step (phase pass -> collision), fp32 store
     float2* nab[2];        // [N] (Na, Nb) per site by step parity, fp16 store: the reference of the
                            //     stored component deviations and the phase pass -> collision hand-off
+    float* drho;           // [N] rho - 1 of each site at the last even step, fp16 store: the
+                           //     reference of the stored momentum deviations
     void* f;               // [19][N] momentum distributions (AA in place)
     void* a;               // [7][N]  component A
     void* b;               // [7][N]  component B
@@ -67,6 +69,7 @@ struct lbpm_ctx {
     int* d_halo_site = nullptr;     // [H]
     float* d_nsum = nullptr;        // [N] fp32 store
     float2* d_nab[2] = {nullptr, nullptr};  // [N] each, fp16 store
+    float* d_drho = nullptr;                // [N] fp16 store
     void* d_f = nullptr;
     void* d_a = nullptr;
     void* d_b = nullptr;

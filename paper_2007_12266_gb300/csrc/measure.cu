@@ -105,6 +105,12 @@ __global__ void __launch_bounds__(kBlock) k_import_ref(DomainView d, int which, 
     if (n >= d.n_sites) return;
     const size_t N = d.n_sites;
     float s = 0.0f;
+    if (which == LBPM_DIST_F) {
+#pragma unroll
+        for (int q = 0; q < Q19; ++q) s += in[q * N + n];
+        d.drho[n] = s - 1.0f;
+        return;
+    }
 #pragma unroll
     for (int q = 0; q < Q7; ++q) s += in[q * N + n];
     float2* ref = d.nab[PAR ^ 1] + n;
@@ -128,7 +134,11 @@ __global__ void __launch_bounds__(kBlock) k_import(DomainView d, int which, cons
     static_for<0, Q19>([&](auto qc) {
         constexpr int q = decltype(qc)::value;
         const size_t i = read_slot<PAR, q>(d, n, nb);
-        if (which == LBPM_DIST_F) S::template st_f<q>(d.f, i, in[q * N + n]);
+        if (which == LBPM_DIST_F) {
+            float val = in[q * N + n];
+            if constexpr (S::kRef) val -= t19(q) * d.drho[f_ref_read<PAR, q>(n, nb)];
+            S::template st_f<q>(d.f, i, val);
+        }
         if constexpr (q < Q7) {
             if (which != LBPM_DIST_F) {
                 float val = in[q * N + n];
@@ -216,7 +226,7 @@ cudaError_t launch_export_dist(const lbpm_ctx* c, int parity, int which, float* 
 }
 
 cudaError_t launch_import_dist(const lbpm_ctx* c, int parity, int which, const float* in, cudaStream_t s) {
-    if (c->params.precision == LBPM_FP16 && which != LBPM_DIST_F && c->N > 0) {
+    if (c->params.precision == LBPM_FP16 && c->N > 0) {
         if (parity == 0) k_import_ref<0><<<blocks_for(c->N), kBlock, 0, s>>>(make_view(c), which, in);
         else k_import_ref<1><<<blocks_for(c->N), kBlock, 0, s>>>(make_view(c), which, in);
         const cudaError_t e = cudaGetLastError();

@@ -23,6 +23,7 @@ __device__ __forceinline__ void load_site(const DomainView& d, int n, float (&f)
     static_for<0, Q19>([&](auto qc) {
         constexpr int q = decltype(qc)::value;
         f[q] = S::template ld_f<q>(d.f, read_slot<PAR, q>(d, n, nb));
+        if constexpr (S::kRef) f[q] = fmaf(t19(q), d.drho[f_ref_read<PAR, q>(n, nb)], f[q]);
     });
     load_components<PAR, S>(d, n, nb, a, b);
 }

@@ -56,13 +56,14 @@ __device__ __forceinline__ float phi0_of_site(const DomainView& d, int n, const 
 }
 
 // fp16 store: densities of the initial state, as if written by a step -1 (the
-// reference of the component deviations read at step 0).
+// reference of the deviations read at step 0).
 __global__ void __launch_bounds__(kBlock) k_init_ref(DomainView d, const float* phi0, int nx, int ny, int px,
                                                      int pxpy) {
     const int n = blockIdx.x * kBlock + threadIdx.x;
     if (n >= d.n_sites) return;
     const float p = phi0_of_site(d, n, phi0, nx, ny, px, pxpy);
     d.nab[1][n] = make_float2(0.5f * (1.0f + p), 0.5f * (1.0f - p));
+    d.drho[n] = 0.0f;   // rho = 1
 }
 
 // Initial state consistent with phi0 (rho = 1, u = 0), written in the even
@@ -117,6 +118,7 @@ DomainView make_view(const lbpm_ctx* c) {
     d.nsum = c->d_nsum;
     d.nab[0] = c->d_nab[0];
     d.nab[1] = c->d_nab[1];
+    d.drho = c->d_drho;
     d.f = c->d_f;
     d.a = c->d_a;
     d.b = c->d_b;

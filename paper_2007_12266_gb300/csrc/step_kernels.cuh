@@ -51,14 +51,23 @@ struct StoreF32 {
     }
 };
 
-// fp16 storage of deviations from the rest-state equilibrium, arithmetic in
-// fp32. Momentum populations: f_q - t_q (rest state rho = 1). Component
-// populations: A_q - w_q Na(s), B_q - w_q Nb(s), where s is the site that
-// wrote the value and Na(s), Nb(s) its densities at that step, kept in fp32
-// per site (DomainView::nab). Storing the values themselves lets every site of
-// a pure phase round the same value the same way on the fp16 grid, a biased
-// error that leaked 3e-3 of the component mass per 1,000 steps; the
-// deviations are small in the bulk, so their rounding is negligible there.
+// fp16 storage of deviations from a local rest-state equilibrium, arithmetic
+// in fp32: f_q - t_q rho(s), A_q - w_q Na(s), B_q - w_q Nb(s), with rho, Na,
+// Nb of a reference site s kept in fp32 per site (DomainView::drho, ::nab).
+// For A, B the reference is the site that wrote the value, at that step. For
+// f it is the writing site for values written at an even step (read at the
+// next odd step through the neighbour table) and the destination site, with
+// its density of the last even step, for values written at an odd step (read
+// at the next even step by that destination with one coalesced load); drho
+// is written only at even steps.
+// Storing A, B themselves let every site of a pure phase round the same value
+// the same way on the fp16 grid, a biased error that leaked 3e-3 of the
+// component mass per 1,000 steps; storing f - t_q left the local density
+// excursion (up to a few 1e-2 under a body force and capillary pressure) in
+// the stored number and cost the velocity its precision. The deviations from
+// the writer's rest state are small, so their rounding is negligible.
+// ld_fdev / st_fdev below exchange the stored number; the kernels add the
+// writer's t_q (rho(s) - 1).
 // Values are scaled by 2^14 (an exact power of two) to keep small deviations
 // out of fp16's subnormal range; |deviation| up to 4 stays representable.
 struct StoreF16 {
@@ -96,6 +105,11 @@ struct StoreF16 {
 // still running. wait_prior_grid() blocks until that kernel has completed and
 // its writes are visible; allow_next_grid() lets the next kernel start its
 // blocks. Without the launch attribute both are no-ops.
+// Data written by an earlier kernel of the step chain (phi, nsum, the
+// fp16 reference densities, the populations) is read with plain coherent
+// loads only: a read-only (__ldg / .nc) load may legally be hoisted by the
+// compiler above wait_prior_grid(), which would read the previous step's
+// values. __ldg is kept for the static index arrays.
 __device__ __forceinline__ void wait_prior_grid() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void allow_next_grid() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
@@ -173,6 +187,14 @@ __device__ __forceinline__ int writer_of(int n, const int* nb) {
     }
 }
 
+// Site whose density is the reference of the momentum population read as
+// direction Q by site n at a step of parity PAR (see StoreF16).
+template <int PAR, int Q>
+__device__ __forceinline__ int f_ref_read(int n, const int* nb) {
+    if constexpr (PAR == 0) return n;
+    else return writer_of<Q>(n, nb);
+}
+
 // A_q, B_q of site n at a step of parity PAR (nb[1..6]: face neighbours).
 template <int PAR, class S>
 __device__ __forceinline__ void load_components(const DomainView& d, int n, const int* nb, float (&a)[Q7],
@@ -183,7 +205,7 @@ __device__ __forceinline__ void load_components(const DomainView& d, int n, cons
         a[q] = S::template ld_c<q>(d.a, i);
         b[q] = S::template ld_c<q>(d.b, i);
         if constexpr (S::kRef) {
-            const float2 r = __ldg(nab_prev<PAR>(d) + writer_of<q>(n, nb));
+            const float2 r = nab_prev<PAR>(d)[writer_of<q>(n, nb)];
             a[q] = fmaf(w7(q), r.x, a[q]);
             b[q] = fmaf(w7(q), r.y, b[q]);
         }
@@ -269,6 +291,7 @@ __device__ __forceinline__ void collide_thread(const DomainView& d, int n) {
     static_for<0, Q19>([&](auto qc) {
         constexpr int q = decltype(qc)::value;
         f[q] = S::template ld_fdev<q>(d.f, read_slot<PAR, q>(d, n, nb));
+        if constexpr (S::kRef) f[q] = fmaf(t19(q), d.drho[f_ref_read<PAR, q>(n, nb)], f[q]);
     });
 
     // Everything above (site and neighbour ids, f from the previous collision)
@@ -278,22 +301,22 @@ __device__ __forceinline__ void collide_thread(const DomainView& d, int n) {
     wait_prior_grid();
 
     // phase field: own value and the 18 neighbours (solids hold phi_s)
-    const float phi_c = __ldg(d.phi + v);
+    const float phi_c = d.phi[v];
     float Na, Nb;
     if constexpr (S::kRef) {
-        const float2 r = __ldg(nab_cur<PAR>(d) + n);
+        const float2 r = nab_cur<PAR>(d)[n];
         Na = r.x;
         Nb = r.y;
     } else {
         // Na = N (1 + phi)/2, Nb = N (1 - phi)/2 with N from the phase pass
-        const float Nt = __ldg(d.nsum + n);
+        const float Nt = d.nsum[n];
         Na = 0.5f * Nt * (1.0f + phi_c);
         Nb = 0.5f * Nt * (1.0f - phi_c);
     }
     float p[Q19];
     static_for<1, Q19>([&](auto qc) {
         constexpr int q = decltype(qc)::value;
-        p[q] = __ldg(d.phi + v + d.off[q]);
+        p[q] = d.phi[v + d.off[q]];
     });
 
     // color gradient C = sum_q g_q xi_q phi(x + xi_q)
@@ -390,10 +413,37 @@ __device__ __forceinline__ void collide_thread(const DomainView& d, int n) {
         const float dmi = fmaf(3.0f * t, xf, -s_m * (fm - eqm));
         const float inc_q = dp + dmi, inc_o = dp - dmi;
         dsum += inc_q + inc_o;
-        S::template st_fdev<q>(d.f, write_slot_v<PAR, q>(d, n, v), f[q] + inc_q);
-        S::template st_fdev<o>(d.f, write_slot_v<PAR, o>(d, n, v), f[o] + inc_o);
+        if constexpr (S::kRef) {
+            // even step: relative to this site's rest state t_q rho; odd step:
+            // relative to the destination's density of the last even step
+            float rq = drho, ro = drho;
+            size_t iq, io;
+            if constexpr (PAR == 0) {
+                iq = write_slot_v<PAR, q>(d, n, v);
+                io = write_slot_v<PAR, o>(d, n, v);
+            } else {
+                const int dq = ld_fresh(d.vsite + v + d.off[q]);
+                const int dd = ld_fresh(d.vsite + v + d.off[o]);
+                const size_t N = static_cast<size_t>(d.n_sites);
+                iq = dq >= 0 ? static_cast<size_t>(q) * N + dq : static_cast<size_t>(o) * N + n;
+                io = dd >= 0 ? static_cast<size_t>(o) * N + dd : static_cast<size_t>(q) * N + n;
+                rq = d.drho[dq >= 0 ? dq : n];
+                ro = d.drho[dd >= 0 ? dd : n];
+            }
+            S::template st_fdev<q>(d.f, iq, fmaf(-t, rq, f[q] + inc_q));
+            S::template st_fdev<o>(d.f, io, fmaf(-t, ro, f[o] + inc_o));
+        } else {
+            S::template st_fdev<q>(d.f, write_slot_v<PAR, q>(d, n, v), f[q] + inc_q);
+            S::template st_fdev<o>(d.f, write_slot_v<PAR, o>(d, n, v), f[o] + inc_o);
+        }
     });
-    S::template st_fdev<0>(d.f, write_slot_v<PAR, 0>(d, n, v), f[0] - dsum);
+    if constexpr (S::kRef) {
+        const float r0 = PAR == 0 ? drho : d.drho[n];
+        S::template st_fdev<0>(d.f, write_slot_v<PAR, 0>(d, n, v), fmaf(-t19(0), r0, f[0] - dsum));
+        if constexpr (PAR == 0) d.drho[n] = drho;
+    } else {
+        S::template st_fdev<0>(d.f, write_slot_v<PAR, 0>(d, n, v), f[0] - dsum);
+    }
 
     // recolored component distributions (Eqs. LBE-mass-a/b), streamed on the
     // fly; the rest populations take the remainder of Na and Nb so that the
@@ -453,12 +503,17 @@ __device__ __forceinline__ void reservoir_thread(const DomainView& d, int n, int
     static_for<0, Q19>([&](auto qc) {
         constexpr int q = decltype(qc)::value;
         const size_t i = read_slot<PAR, q>(d, n, nb);
-        S::template st_f<q>(d.f, i, t19(q) * rho);
+        if constexpr (S::kRef) {
+            const float dw = d.drho[f_ref_read<PAR, q>(n, nb)];
+            S::template st_fdev<q>(d.f, i, t19(q) * (rho - 1.0f - dw));
+        } else {
+            S::template st_f<q>(d.f, i, t19(q) * rho);
+        }
         if constexpr (q < Q7) {
             float av = w7(q) * na, bv = w7(q) * (1.0f - na);
             if constexpr (S::kRef) {
                 // the next step reconstructs with the writer's densities of this step
-                const float2 r = __ldg(nab_prev<PAR>(d) + writer_of<q>(n, nb));
+                const float2 r = nab_prev<PAR>(d)[writer_of<q>(n, nb)];
                 av -= w7(q) * r.x;
                 bv -= w7(q) * r.y;
             }
