@@ -44,15 +44,19 @@ __global__ void __launch_bounds__(BT) k_batch_phase(const DomainView* views, con
 }
 
 template <int PAR, class S, int BT>
-__global__ void __launch_bounds__(BT) k_batch_collide(const DomainView* views, const BatchTile* tiles, int n_tiles) {
+__global__ void __launch_bounds__(BT, 1024 / BT) k_batch_collide(const DomainView* views, const BatchTile* tiles, int n_tiles) {
     __shared__ DomainView sv;
+    constexpr int kSlots = PAR == 1 ? (Q19 - 1) * BT : 1;
+    constexpr int kRefs = PAR == 1 && S::kRef ? (Q19 - 1) * BT : 1;
+    __shared__ int slot[kSlots];
+    __shared__ float ref[kRefs];
     for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
         const BatchTile tl = tiles[t];
         if (threadIdx.x < static_cast<int>(sizeof(DomainView) / sizeof(int)))
             reinterpret_cast<int*>(&sv)[threadIdx.x] = reinterpret_cast<const int*>(views + tl.job)[threadIdx.x];
         __syncthreads();
         const int n = tl.first + threadIdx.x;
-        if (n < sv.n_sites) collide_thread<PAR, S>(sv, n);
+        if (n < sv.n_sites) collide_thread<PAR, S>(sv, n, SlotCache{slot + threadIdx.x, ref + threadIdx.x, BT});
         __syncthreads();
     }
 }

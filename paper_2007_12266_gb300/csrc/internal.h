@@ -35,6 +35,7 @@ struct DomainView {
     void* b;               // [7][N]  component B
     float tau_a, tau_b, alpha, beta;
     float fx, fy, fz;
+    float fterm[9];        // 3 t_q xi_q . F of the odd directions q = 2k + 1 (forcing term per pair)
     float s_nu, s_m;       // rates when tau_a == tau_b
     int uniform_tau;
 };

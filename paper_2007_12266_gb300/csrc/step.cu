@@ -31,9 +31,14 @@ __global__ void __launch_bounds__(kBlock) k_phase(DomainView d) {
 }
 
 template <int PAR, class S>
-__global__ void __launch_bounds__(kBlock) k_collide(DomainView d) {
+__global__ void __launch_bounds__(kBlock, 4) k_collide(DomainView d) {
+    // odd steps: slot (and fp16 reference) cache, see SlotCache
+    constexpr int kSlots = PAR == 1 ? (Q19 - 1) * kBlock : 1;
+    constexpr int kRefs = PAR == 1 && S::kRef ? (Q19 - 1) * kBlock : 1;
+    __shared__ int slot[kSlots];
+    __shared__ float ref[kRefs];
     const int n = blockIdx.x * kBlock + threadIdx.x;
-    if (n < d.n_sites) collide_thread<PAR, S>(d, n);
+    if (n < d.n_sites) collide_thread<PAR, S>(d, n, SlotCache{slot + threadIdx.x, ref + threadIdx.x, kBlock});
 }
 
 template <int PAR, class S>
@@ -130,6 +135,10 @@ DomainView make_view(const lbpm_ctx* c) {
     d.fx = static_cast<float>(p.force[0]);
     d.fy = static_cast<float>(p.force[1]);
     d.fz = static_cast<float>(p.force[2]);
+    for (int k = 0; k < 9; ++k) {
+        const int q = 2 * k + 1;
+        d.fterm[k] = 3.0f * t19(q) * (cx(q) * d.fx + cy(q) * d.fy + cz(q) * d.fz);
+    }
     d.uniform_tau = p.tau_a == p.tau_b;
     const float s_nu = 1.0f / static_cast<float>(p.tau_a);
     d.s_nu = s_nu;

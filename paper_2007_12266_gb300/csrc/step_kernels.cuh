@@ -24,7 +24,15 @@ namespace lbm {
 // Plain fp32 storage. ld_fdev / st_fdev exchange deviations f_q - t_q from
 // the rest state, which the collision works with.
 struct StoreF32 {
+    using T = float;
     static constexpr bool kRef = false;   // component values stored as they are
+    // pointer forms (hot path): p points at the slot itself
+    template <int Q>
+    static __device__ __forceinline__ float ld_fdev(const T* p) { return *p - t19(Q); }
+    template <int Q>
+    static __device__ __forceinline__ void st_fdev(T* p, float dev) { *p = t19(Q) + dev; }
+    static __device__ __forceinline__ float ld_c(const T* p) { return *p; }
+    static __device__ __forceinline__ void st_c(T* p, float v) { *p = v; }
     template <int Q>
     static __device__ __forceinline__ float ld_fdev(const void* p, size_t i) {
         return static_cast<const float*>(p)[i] - t19(Q);
@@ -71,9 +79,16 @@ struct StoreF32 {
 // Values are scaled by 2^14 (an exact power of two) to keep small deviations
 // out of fp16's subnormal range; |deviation| up to 4 stays representable.
 struct StoreF16 {
+    using T = __half;
     static constexpr bool kRef = true;
     static constexpr float kScale = 16384.0f;
     static constexpr float kInv = 1.0f / 16384.0f;
+    template <int Q>
+    static __device__ __forceinline__ float ld_fdev(const T* p) { return __half2float(*p) * kInv; }
+    template <int Q>
+    static __device__ __forceinline__ void st_fdev(T* p, float dev) { *p = __float2half_rn(dev * kScale); }
+    static __device__ __forceinline__ float ld_c(const T* p) { return __half2float(*p) * kInv; }
+    static __device__ __forceinline__ void st_c(T* p, float v) { *p = __float2half_rn(v * kScale); }
     template <int Q>
     static __device__ __forceinline__ float ld_fdev(const void* p, size_t i) {
         return __half2float(static_cast<const __half*>(p)[i]) * kInv;
@@ -113,15 +128,6 @@ struct StoreF16 {
 __device__ __forceinline__ void wait_prior_grid() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void allow_next_grid() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
-// Read-only load that the compiler may not merge with an earlier load of the
-// same address: re-reading a neighbour id from L1 is cheaper than keeping 18
-// of them live in registers across the collision.
-__device__ __forceinline__ int ld_fresh(const int* p) {
-    int v;
-    asm volatile("ld.global.nc.b32 %0, [%1];" : "=r"(v) : "l"(p));
-    return v;
-}
-
 // ---------------------------------------------------------------------------
 // AA read map: where the value of direction Q of site n lives at a step of
 // parity PAR (the same slot the step writes direction opp(Q) to).
@@ -135,35 +141,6 @@ __device__ __forceinline__ size_t read_slot(const DomainView& d, int n, const in
         // upstream site x - xi_Q = x + xi_opp(Q), or -1 (bounce-back)
         const int up = nb[opp(Q)];
         return up >= 0 ? static_cast<size_t>(opp(Q)) * N + up : static_cast<size_t>(Q) * N + n;
-    }
-}
-
-template <int PAR, int Q>
-__device__ __forceinline__ size_t write_slot(const DomainView& d, int n, const int* nb) {
-    (void)nb;
-    const size_t N = static_cast<size_t>(d.n_sites);
-    if constexpr (Q == 0) {
-        return static_cast<size_t>(n);
-    } else if constexpr (PAR == 0) {
-        return static_cast<size_t>(opp(Q)) * N + n;
-    } else {
-        // downstream site x + xi_Q, or -1 (halfway bounce-back)
-        const int down = nb[Q];
-        return down >= 0 ? static_cast<size_t>(Q) * N + down : static_cast<size_t>(opp(Q)) * N + n;
-    }
-}
-
-// write slot with the downstream neighbour re-read from the padded site grid
-template <int PAR, int Q>
-__device__ __forceinline__ size_t write_slot_v(const DomainView& d, int n, int v) {
-    const size_t N = static_cast<size_t>(d.n_sites);
-    if constexpr (Q == 0) {
-        return static_cast<size_t>(n);
-    } else if constexpr (PAR == 0) {
-        return static_cast<size_t>(opp(Q)) * N + n;
-    } else {
-        const int down = ld_fresh(d.vsite + v + d.off[Q]);
-        return down >= 0 ? static_cast<size_t>(Q) * N + down : static_cast<size_t>(opp(Q)) * N + n;
     }
 }
 
@@ -271,38 +248,60 @@ __device__ __forceinline__ void phase_thread(const DomainView& d, int t) {
 // ---------------------------------------------------------------------------
 // fused collide + stream                                            Sec. 3.1
 // ---------------------------------------------------------------------------
-template <int PAR, class S>
-__device__ __forceinline__ void collide_thread(const DomainView& d, int n) {
-    const int v = __ldg(d.site_vox + n);
+// At an odd step site n reads direction opp(q) from, and writes direction q
+// to, the same slot: row q at the downstream neighbour x + xi_q, or row
+// opp(q) at n itself when that voxel is solid. With fp16 storage both also
+// use the same density reference (that neighbour's density of the last even
+// step, which odd steps do not change). SlotCache keeps the slot (relative to
+// row q, a signed 32-bit offset) and the reference of each direction between
+// the gather and the scatter, in shared memory laid out [q - 1][thread] so
+// that a warp's accesses fall in distinct banks.
+struct SlotCache {
+    int* slot;      // entry of direction 1 of this thread; direction q at slot[(q - 1) * stride]
+    float* ref;     // same layout (fp16 storage only)
+    int stride;     // threads per block
+};
 
-    // neighbour sites for the odd-step gather / scatter
-    int nb[Q19];
-    if constexpr (PAR == 1) {
-        static_for<1, Q19>([&](auto qc) {
+// Incoming distributions of site n (voxel v), as deviations d_q = f_q - t_q
+// from the rest state (exact in fp32 near rest), so that density and
+// momentum are sums of small numbers and the relaxation acts on small
+// quantities. Odd steps also fill the slot cache.
+template <int PAR, class S>
+__device__ __forceinline__ void load_f(const DomainView& d, int n, int v, float (&f)[Q19], SlotCache sc) {
+    const int Ni = d.n_sites;
+    const size_t N = static_cast<size_t>(Ni);
+    const typename S::T* const F = static_cast<const typename S::T*>(d.f);
+    if constexpr (PAR == 0) {
+        // even step: own slots, row q; fp16 references are all this site's
+        float r = 0.0f;
+        if constexpr (S::kRef) r = d.drho[n];
+        static_for<0, Q19>([&](auto qc) {
             constexpr int q = decltype(qc)::value;
-            nb[q] = __ldg(d.vsite + v + d.off[q]);
+            f[q] = S::template ld_fdev<q>(F + q * N + n);
+            if constexpr (S::kRef) f[q] = fmaf(t19(q), r, f[q]);
+        });
+    } else {
+        f[0] = S::template ld_fdev<0>(F + n);
+        if constexpr (S::kRef) f[0] = fmaf(t19(0), d.drho[n], f[0]);
+        static_for<1, Q19>([&](auto qc) {
+            constexpr int q = decltype(qc)::value;   // direction of the downstream slot
+            constexpr int o = opp(q);                // direction read from it
+            const int m = __ldg(d.vsite + v + d.off[q]);
+            const int s = m >= 0 ? m : n + (o - q) * Ni;
+            sc.slot[(q - 1) * sc.stride] = s;
+            f[o] = S::template ld_fdev<o>(F + q * N + s);
+            if constexpr (S::kRef) {
+                const float r = d.drho[m >= 0 ? m : n];
+                sc.ref[(q - 1) * sc.stride] = r;
+                f[o] = fmaf(t19(o), r, f[o]);
+            }
         });
     }
+}
 
-    // incoming distributions, as deviations d_q = f_q - t_q from the rest
-    // state (exact in fp32 near rest), so that density and momentum are sums of
-    // small numbers and the relaxation acts on small quantities
-    float f[Q19];
-    static_for<0, Q19>([&](auto qc) {
-        constexpr int q = decltype(qc)::value;
-        f[q] = S::template ld_fdev<q>(d.f, read_slot<PAR, q>(d, n, nb));
-        if constexpr (S::kRef) f[q] = fmaf(t19(q), d.drho[f_ref_read<PAR, q>(n, nb)], f[q]);
-    });
-
-    // Everything above (site and neighbour ids, f from the previous collision)
-    // is safe to read before the phase pass of this step completes; phi and
-    // nsum are its outputs, and the A/B slots written below are its inputs.
-    allow_next_grid();
-    wait_prior_grid();
-
-    // phase field: own value and the 18 neighbours (solids hold phi_s)
-    const float phi_c = d.phi[v];
-    float Na, Nb;
+// Na, Nb of site n from the phase pass of this step.
+template <int PAR, class S>
+__device__ __forceinline__ void site_nab(const DomainView& d, int n, float phi_c, float& Na, float& Nb) {
     if constexpr (S::kRef) {
         const float2 r = nab_cur<PAR>(d)[n];
         Na = r.x;
@@ -313,21 +312,56 @@ __device__ __forceinline__ void collide_thread(const DomainView& d, int n) {
         Na = 0.5f * Nt * (1.0f + phi_c);
         Nb = 0.5f * Nt * (1.0f - phi_c);
     }
-    float p[Q19];
-    static_for<1, Q19>([&](auto qc) {
-        constexpr int q = decltype(qc)::value;
-        p[q] = d.phi[v + d.off[q]];
-    });
+}
 
-    // color gradient C = sum_q g_q xi_q phi(x + xi_q)
-    float Cx = 0.0f, Cy = 0.0f, Cz = 0.0f;
+// colour gradient C = sum_q g_q xi_q phi(x + xi_q); phi_at(q) gives the
+// neighbour's phase (solids hold phi_s)
+template <class PhiAt>
+__device__ __forceinline__ void color_gradient(PhiAt&& phi_at, float& Cx, float& Cy, float& Cz) {
+    Cx = 0.0f;
+    Cy = 0.0f;
+    Cz = 0.0f;
     static_for<1, Q19>([&](auto qc) {
         constexpr int q = decltype(qc)::value;
         constexpr float g = grad_w(q);
-        if constexpr (cx(q) != 0) Cx = fmaf(g * cx(q), p[q], Cx);
-        if constexpr (cy(q) != 0) Cy = fmaf(g * cy(q), p[q], Cy);
-        if constexpr (cz(q) != 0) Cz = fmaf(g * cz(q), p[q], Cz);
+        const float p = phi_at(qc);
+        if constexpr (cx(q) != 0) Cx = fmaf(g * cx(q), p, Cx);
+        if constexpr (cy(q) != 0) Cy = fmaf(g * cy(q), p, Cy);
+        if constexpr (cz(q) != 0) Cz = fmaf(g * cz(q), p, Cz);
     });
+}
+
+// macroscopic moments: drho = rho - 1 and j from the deviations
+struct Moments {
+    float drho, jx, jy, jz;
+};
+__device__ __forceinline__ Moments moments(const float (&f)[Q19]) {
+    Moments m{0.0f, 0.0f, 0.0f, 0.0f};
+    static_for<0, Q19>([&](auto qc) {
+        constexpr int q = decltype(qc)::value;
+        m.drho += f[q];
+        if constexpr (cx(q) > 0) m.jx += f[q];
+        if constexpr (cx(q) < 0) m.jx -= f[q];
+        if constexpr (cy(q) > 0) m.jy += f[q];
+        if constexpr (cy(q) < 0) m.jy -= f[q];
+        if constexpr (cz(q) > 0) m.jz += f[q];
+        if constexpr (cz(q) < 0) m.jz -= f[q];
+    });
+    return m;
+}
+
+// Collision, recoloring and streaming of site n, given its incoming
+// deviations f and their moments, its phase phi_c, Na, Nb and the colour
+// gradient.
+template <int PAR, class S>
+__device__ __forceinline__ void collide_site(const DomainView& d, int n, const float (&f)[Q19], Moments mo,
+                                             float phi_c, float Na, float Nb, float Cx, float Cy, float Cz,
+                                             SlotCache sc) {
+    using T = typename S::T;
+    const size_t N = static_cast<size_t>(d.n_sites);
+    T* const F = static_cast<T*>(d.f);
+    const float drho = mo.drho, jx = mo.jx, jy = mo.jy, jz = mo.jz;
+
     const float C2 = Cx * Cx + Cy * Cy + Cz * Cz;
     float nx = 0.0f, ny = 0.0f, nz = 0.0f, Cmag = 0.0f;
     if (C2 > 0.0f) {
@@ -337,19 +371,6 @@ __device__ __forceinline__ void collide_thread(const DomainView& d, int n) {
         ny = Cy * inv;
         nz = Cz * inv;
     }
-
-    // macroscopic moments: drho = rho - 1 and j from the deviations
-    float drho = 0.0f, jx = 0.0f, jy = 0.0f, jz = 0.0f;
-    static_for<0, Q19>([&](auto qc) {
-        constexpr int q = decltype(qc)::value;
-        drho += f[q];
-        if constexpr (cx(q) > 0) jx += f[q];
-        if constexpr (cx(q) < 0) jx -= f[q];
-        if constexpr (cy(q) > 0) jy += f[q];
-        if constexpr (cy(q) < 0) jy -= f[q];
-        if constexpr (cz(q) > 0) jz += f[q];
-        if constexpr (cz(q) < 0) jz -= f[q];
-    });
 
     // relaxation rates from the viscosity (tau mixed linearly in phi)
     float s_nu = d.s_nu, s_m = d.s_m;
@@ -387,6 +408,14 @@ __device__ __forceinline__ void collide_thread(const DomainView& d, int n) {
     const float bxa = d.beta * 0.5f * (1.0f - phi_c);
     const float bxb = d.beta * 0.5f * (1.0f + phi_c);
 
+    // destination of direction q (q >= 1): row opp(q) at n (even step) or
+    // the cached slot of row q (odd step)
+    auto dst = [&](auto qc, auto* base) {
+        constexpr int q = decltype(qc)::value;
+        if constexpr (PAR == 0) return base + opp(q) * N + n;
+        else return base + q * N + sc.slot[(q - 1) * sc.stride];
+    };
+
     // The increments of the moving populations sum to minus the rest
     // increment in exact arithmetic; taking the rest increment as that sum
     // keeps fp32 mass exact up to unbiased rounding.
@@ -395,10 +424,10 @@ __device__ __forceinline__ void collide_thread(const DomainView& d, int n) {
         constexpr int q = 2 * decltype(pc)::value + 1;   // q odd, opp(q) = q + 1
         constexpr int o = q + 1;
         constexpr float t = t19(q);
-        float cu = 0.0f, xf = 0.0f;
-        if constexpr (cx(q) != 0) { cu += cx(q) * jx; xf += cx(q) * d.fx; }
-        if constexpr (cy(q) != 0) { cu += cy(q) * jy; xf += cy(q) * d.fy; }
-        if constexpr (cz(q) != 0) { cu += cz(q) * jz; xf += cz(q) * d.fz; }
+        float cu = 0.0f;
+        if constexpr (cx(q) != 0) cu += cx(q) * jx;
+        if constexpr (cy(q) != 0) cu += cy(q) * jy;
+        if constexpr (cz(q) != 0) cu += cz(q) * jz;
         float eqp = t * fmaf(4.5f * cu, cu, drho_iso);
         static_for<1, 16>([&](auto kc) {
             constexpr int k = decltype(kc)::value;
@@ -410,39 +439,30 @@ __device__ __forceinline__ void collide_thread(const DomainView& d, int n) {
         const float fp = 0.5f * (f[q] + f[o]);
         const float fm = 0.5f * (f[q] - f[o]);
         const float dp = -s_nu * (fp - eqp);
-        const float dmi = fmaf(3.0f * t, xf, -s_m * (fm - eqm));
+        const float dmi = fmaf(-s_m, fm - eqm, d.fterm[q >> 1]);
         const float inc_q = dp + dmi, inc_o = dp - dmi;
         dsum += inc_q + inc_o;
+        float vq = f[q] + inc_q, vo = f[o] + inc_o;
         if constexpr (S::kRef) {
             // even step: relative to this site's rest state t_q rho; odd step:
             // relative to the destination's density of the last even step
-            float rq = drho, ro = drho;
-            size_t iq, io;
             if constexpr (PAR == 0) {
-                iq = write_slot_v<PAR, q>(d, n, v);
-                io = write_slot_v<PAR, o>(d, n, v);
+                vq = fmaf(-t, drho, vq);
+                vo = fmaf(-t, drho, vo);
             } else {
-                const int dq = ld_fresh(d.vsite + v + d.off[q]);
-                const int dd = ld_fresh(d.vsite + v + d.off[o]);
-                const size_t N = static_cast<size_t>(d.n_sites);
-                iq = dq >= 0 ? static_cast<size_t>(q) * N + dq : static_cast<size_t>(o) * N + n;
-                io = dd >= 0 ? static_cast<size_t>(o) * N + dd : static_cast<size_t>(q) * N + n;
-                rq = d.drho[dq >= 0 ? dq : n];
-                ro = d.drho[dd >= 0 ? dd : n];
+                vq = fmaf(-t, sc.ref[(q - 1) * sc.stride], vq);
+                vo = fmaf(-t, sc.ref[(o - 1) * sc.stride], vo);
             }
-            S::template st_fdev<q>(d.f, iq, fmaf(-t, rq, f[q] + inc_q));
-            S::template st_fdev<o>(d.f, io, fmaf(-t, ro, f[o] + inc_o));
-        } else {
-            S::template st_fdev<q>(d.f, write_slot_v<PAR, q>(d, n, v), f[q] + inc_q);
-            S::template st_fdev<o>(d.f, write_slot_v<PAR, o>(d, n, v), f[o] + inc_o);
         }
+        S::template st_fdev<q>(dst(std::integral_constant<int, q>{}, F), vq);
+        S::template st_fdev<o>(dst(std::integral_constant<int, o>{}, F), vo);
     });
     if constexpr (S::kRef) {
         const float r0 = PAR == 0 ? drho : d.drho[n];
-        S::template st_fdev<0>(d.f, write_slot_v<PAR, 0>(d, n, v), fmaf(-t19(0), r0, f[0] - dsum));
+        S::template st_fdev<0>(F + n, fmaf(-t19(0), r0, f[0] - dsum));
         if constexpr (PAR == 0) d.drho[n] = drho;
     } else {
-        S::template st_fdev<0>(d.f, write_slot_v<PAR, 0>(d, n, v), f[0] - dsum);
+        S::template st_fdev<0>(F + n, f[0] - dsum);
     }
 
     // recolored component distributions (Eqs. LBE-mass-a/b), streamed on the
@@ -450,6 +470,8 @@ __device__ __forceinline__ void collide_thread(const DomainView& d, int n) {
     // fp32 weights (whose sum is not exactly 1) create no mass. With fp16
     // storage the stored quantity is the deviation from w_q Na (w_q Nb), which
     // the formula gives directly: w_q Na (4.5 u.xi + beta Nb/N n.xi).
+    T* const A = static_cast<T*>(d.a);
+    T* const B = static_cast<T*>(d.b);
     float asum = 0.0f, bsum = 0.0f;
     static_for<1, Q7>([&](auto qc) {
         constexpr int q = decltype(qc)::value;
@@ -469,18 +491,37 @@ __device__ __forceinline__ void collide_thread(const DomainView& d, int n) {
         }
         asum += av;
         bsum += bv;
-        const size_t i = write_slot_v<PAR, q>(d, n, v);
-        S::template st_c<q>(d.a, i, av);
-        S::template st_c<q>(d.b, i, bv);
+        S::st_c(dst(qc, A), av);
+        S::st_c(dst(qc, B), bv);
     });
-    const size_t i0 = write_slot_v<PAR, 0>(d, n, v);
     if constexpr (S::kRef) {
-        S::template st_c<0>(d.a, i0, -asum);
-        S::template st_c<0>(d.b, i0, -bsum);
+        S::st_c(A + n, -asum);
+        S::st_c(B + n, -bsum);
     } else {
-        S::template st_c<0>(d.a, i0, Na - asum);
-        S::template st_c<0>(d.b, i0, Nb - bsum);
+        S::st_c(A + n, Na - asum);
+        S::st_c(B + n, Nb - bsum);
     }
+}
+
+// One site per thread, direct loads.
+template <int PAR, class S>
+__device__ __forceinline__ void collide_thread(const DomainView& d, int n, SlotCache sc) {
+    const int v = __ldg(d.site_vox + n);
+    float f[Q19];
+    load_f<PAR, S>(d, n, v, f, sc);
+
+    // Everything above (site and neighbour ids, f from the previous collision)
+    // is safe to read before the phase pass of this step completes; phi and
+    // nsum are its outputs, and the A/B slots written below are its inputs.
+    allow_next_grid();
+    wait_prior_grid();
+
+    const float* pv = d.phi + v;
+    const float phi_c = *pv;
+    float Na, Nb, Cx, Cy, Cz;
+    site_nab<PAR, S>(d, n, phi_c, Na, Nb);
+    color_gradient([&](auto qc) { return pv[d.off[decltype(qc)::value]]; }, Cx, Cy, Cz);
+    collide_site<PAR, S>(d, n, f, moments(f), phi_c, Na, Nb, Cx, Cy, Cz, sc);
 }
 
 // ---------------------------------------------------------------------------
