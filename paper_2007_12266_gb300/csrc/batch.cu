@@ -30,16 +30,29 @@ namespace {
 
 constexpr int kMaxBlocksPerSm = 16;
 
+// Blocks walk the tile list round-robin (tile blockIdx.x, then + gridDim.x,
+// ...), so the tiles in flight at any moment are neighbours in the list and
+// their phi stencils and neighbour ids share L2 lines; a block reloads the
+// job's view into shared memory only when its next tile belongs to another
+// job.
+__device__ __forceinline__ void load_view(DomainView& sv, const DomainView* views, int job) {
+    __syncthreads();   // every thread is done with the previous view
+    if (threadIdx.x < static_cast<int>(sizeof(DomainView) / sizeof(int)))
+        reinterpret_cast<int*>(&sv)[threadIdx.x] = reinterpret_cast<const int*>(views + job)[threadIdx.x];
+    __syncthreads();
+}
+
 template <int PAR, class S, int BT>
 __global__ void __launch_bounds__(BT) k_batch_phase(const DomainView* views, const BatchTile* tiles, int n_tiles) {
     __shared__ DomainView sv;
+    int job = -1;
     for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
         const BatchTile tl = tiles[t];
-        if (threadIdx.x < static_cast<int>(sizeof(DomainView) / sizeof(int)))
-            reinterpret_cast<int*>(&sv)[threadIdx.x] = reinterpret_cast<const int*>(views + tl.job)[threadIdx.x];
-        __syncthreads();
+        if (tl.job != job) {
+            load_view(sv, views, tl.job);
+            job = tl.job;
+        }
         phase_thread<PAR, S>(sv, tl.first + threadIdx.x);
-        __syncthreads();
     }
 }
 
@@ -50,14 +63,15 @@ __global__ void __launch_bounds__(BT, 1024 / BT) k_batch_collide(const DomainVie
     constexpr int kRefs = PAR == 1 && S::kRef ? (Q19 - 1) * BT : 1;
     __shared__ int slot[kSlots];
     __shared__ float ref[kRefs];
+    int job = -1;
     for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
         const BatchTile tl = tiles[t];
-        if (threadIdx.x < static_cast<int>(sizeof(DomainView) / sizeof(int)))
-            reinterpret_cast<int*>(&sv)[threadIdx.x] = reinterpret_cast<const int*>(views + tl.job)[threadIdx.x];
-        __syncthreads();
+        if (tl.job != job) {
+            load_view(sv, views, tl.job);
+            job = tl.job;
+        }
         const int n = tl.first + threadIdx.x;
         if (n < sv.n_sites) collide_thread<PAR, S>(sv, n, SlotCache{slot + threadIdx.x, ref + threadIdx.x, BT});
-        __syncthreads();
     }
 }
 

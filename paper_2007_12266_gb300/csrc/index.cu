@@ -227,7 +227,7 @@ __global__ void k_export_index(const int* site_vox, const int* vsite, long long 
         site2vox[n] = (X - 1) + static_cast<long long>(nx) * ((Y - 1) + static_cast<long long>(ny) * (Z - 1));
     }
     if (nbr) {
-        for (int q = 1; q < Q19; ++q) nbr[static_cast<long long>(q - 1) * N + n] = vsite[pv + d.off[q]];
+        for (int q = 1; q < Q19; ++q) nbr[static_cast<long long>(q - 1) * N + n] = vsite[pv + stencil_off(d, q)];
     }
 }
 

@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "../../include/lbpm.h"
+#include "lattice.cuh"
 
 namespace lbm {
 
@@ -19,7 +20,7 @@ namespace lbm {
 struct DomainView {
     int n_sites;        // N: pore sites
     int n_halo;         // H: halo voxels that mirror a pore site
-    int off[19];        // padded-grid offset of xi_q
+    int px, pxpy;       // padded-grid strides in y and z: xi_q is at offset cx + cy px + cz pxpy
     const int* site_vox;   // [N] padded voxel of each site
     const int* vsite;      // [Vp] site id, -1 for solid / wall
     float* phi;            // [Vp] phase field; solids hold phi_s, walls 0
@@ -35,10 +36,16 @@ struct DomainView {
     void* b;               // [7][N]  component B
     float tau_a, tau_b, alpha, beta;
     float fx, fy, fz;
-    float fterm[9];        // 3 t_q xi_q . F of the odd directions q = 2k + 1 (forcing term per pair)
+    float fterm[9];        // 3 t_q xi_q . F of the odd directions q = 2k + 1 (forcing term per pair), in
+                           // the collision's working units (times 2^14 with fp16 storage)
     float s_nu, s_m;       // rates when tau_a == tau_b
     int uniform_tau;
 };
+
+// offset of x + xi_q from x in the view's padded grids
+__host__ __device__ __forceinline__ int stencil_off(const DomainView& d, int q) {
+    return stencil_offset(q, d.px, d.pxpy);
+}
 
 struct Allocation {
     void* ptr;

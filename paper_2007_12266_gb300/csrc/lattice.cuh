@@ -27,7 +27,13 @@ __host__ __device__ constexpr int cz(int q) {
     constexpr int t[Q19] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1};
     return t[q];
 }
+// Offset of voxel x + xi_q from x in a padded grid with strides 1, px, pxpy
+// (with a compile-time q the direction's components fold into the code).
+__host__ __device__ constexpr int stencil_offset(int q, int px, int pxpy);
 __host__ __device__ constexpr int opp(int q) { return q == 0 ? 0 : ((q & 1) ? q + 1 : q - 1); }
+__host__ __device__ constexpr int stencil_offset(int q, int px, int pxpy) {
+    return cx(q) + cy(q) * px + cz(q) * pxpy;
+}
 __host__ __device__ constexpr int c2(int q) { return cx(q) * cx(q) + cy(q) * cy(q) + cz(q) * cz(q); }
 
 // D3Q19 weight t_q and D3Q7 weight w_q

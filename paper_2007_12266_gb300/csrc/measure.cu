@@ -127,7 +127,7 @@ __global__ void __launch_bounds__(kBlock) k_import(DomainView d, int which, cons
     if constexpr (PAR == 1 || S::kRef) {
         static_for<1, Q19>([&](auto qc) {
             constexpr int q = decltype(qc)::value;
-            nb[q] = __ldg(d.vsite + v + d.off[q]);
+            nb[q] = __ldg(d.vsite + v + stencil_off(d, q));
         });
     }
     const size_t N = d.n_sites;

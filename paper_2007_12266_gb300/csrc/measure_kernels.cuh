@@ -17,7 +17,7 @@ __device__ __forceinline__ void load_site(const DomainView& d, int n, float (&f)
     if constexpr (PAR == 1 || S::kRef) {
         static_for<1, Q19>([&](auto qc) {
             constexpr int q = decltype(qc)::value;
-            nb[q] = __ldg(d.vsite + v + d.off[q]);
+            nb[q] = __ldg(d.vsite + v + stencil_off(d, q));
         });
     }
     static_for<0, Q19>([&](auto qc) {

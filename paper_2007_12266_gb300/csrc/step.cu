@@ -85,7 +85,7 @@ __global__ void __launch_bounds__(kBlock) k_init(DomainView d, const float* phi0
         const int v = d.site_vox[n];
         static_for<1, Q7>([&](auto qc) {
             constexpr int q = decltype(qc)::value;
-            nbr[q] = __ldg(d.vsite + v + d.off[q]);
+            nbr[q] = __ldg(d.vsite + v + stencil_off(d, q));
         });
     }
     const size_t N = d.n_sites;
@@ -113,8 +113,8 @@ DomainView make_view(const lbpm_ctx* c) {
     DomainView d{};
     d.n_sites = static_cast<int>(c->N);
     d.n_halo = static_cast<int>(c->H);
-    for (int q = 0; q < Q19; ++q)
-        d.off[q] = cx(q) + cy(q) * c->px + cz(q) * c->px * c->py;
+    d.px = static_cast<int>(c->px);
+    d.pxpy = static_cast<int>(c->px * c->py);
     d.site_vox = c->d_site_vox;
     d.vsite = c->d_vsite;
     d.phi = c->d_phi;
@@ -135,9 +135,10 @@ DomainView make_view(const lbpm_ctx* c) {
     d.fx = static_cast<float>(p.force[0]);
     d.fy = static_cast<float>(p.force[1]);
     d.fz = static_cast<float>(p.force[2]);
+    const float K = p.precision == LBPM_FP16 ? StoreF16::kK : StoreF32::kK;
     for (int k = 0; k < 9; ++k) {
         const int q = 2 * k + 1;
-        d.fterm[k] = 3.0f * t19(q) * (cx(q) * d.fx + cy(q) * d.fy + cz(q) * d.fz);
+        d.fterm[k] = K * (3.0f * t19(q) * (cx(q) * d.fx + cy(q) * d.fy + cz(q) * d.fz));
     }
     d.uniform_tau = p.tau_a == p.tau_b;
     const float s_nu = 1.0f / static_cast<float>(p.tau_a);

@@ -26,13 +26,14 @@ namespace lbm {
 struct StoreF32 {
     using T = float;
     static constexpr bool kRef = false;   // component values stored as they are
-    // pointer forms (hot path): p points at the slot itself
+    // Hot-path forms: p points at the slot itself and values are in the
+    // collision's working units, deviations times kK (here 1).
+    static constexpr float kK = 1.0f;
     template <int Q>
-    static __device__ __forceinline__ float ld_fdev(const T* p) { return *p - t19(Q); }
+    static __device__ __forceinline__ float ld_fs(const T* p) { return *p - t19(Q); }
     template <int Q>
-    static __device__ __forceinline__ void st_fdev(T* p, float dev) { *p = t19(Q) + dev; }
-    static __device__ __forceinline__ float ld_c(const T* p) { return *p; }
-    static __device__ __forceinline__ void st_c(T* p, float v) { *p = v; }
+    static __device__ __forceinline__ void st_fs(T* p, float dev) { *p = t19(Q) + dev; }
+    static __device__ __forceinline__ void st_cs(T* p, float v) { *p = v; }
     template <int Q>
     static __device__ __forceinline__ float ld_fdev(const void* p, size_t i) {
         return static_cast<const float*>(p)[i] - t19(Q);
@@ -83,12 +84,15 @@ struct StoreF16 {
     static constexpr bool kRef = true;
     static constexpr float kScale = 16384.0f;
     static constexpr float kInv = 1.0f / 16384.0f;
+    // Hot-path forms: the collision works in units of 2^-14 (kK = 2^14 times
+    // the deviations), so the stored number is used as it is and the scale
+    // costs no multiplication per value.
+    static constexpr float kK = kScale;
     template <int Q>
-    static __device__ __forceinline__ float ld_fdev(const T* p) { return __half2float(*p) * kInv; }
+    static __device__ __forceinline__ float ld_fs(const T* p) { return __half2float(*p); }
     template <int Q>
-    static __device__ __forceinline__ void st_fdev(T* p, float dev) { *p = __float2half_rn(dev * kScale); }
-    static __device__ __forceinline__ float ld_c(const T* p) { return __half2float(*p) * kInv; }
-    static __device__ __forceinline__ void st_c(T* p, float v) { *p = __float2half_rn(v * kScale); }
+    static __device__ __forceinline__ void st_fs(T* p, float v) { *p = __float2half_rn(v); }
+    static __device__ __forceinline__ void st_cs(T* p, float v) { *p = __float2half_rn(v); }
     template <int Q>
     static __device__ __forceinline__ float ld_fdev(const void* p, size_t i) {
         return __half2float(static_cast<const __half*>(p)[i]) * kInv;
@@ -219,7 +223,7 @@ __device__ __forceinline__ void phase_thread(const DomainView& d, int t) {
         if constexpr (need_face_nb<PAR, S>()) {
             static_for<1, 7>([&](auto qc) {
                 constexpr int q = decltype(qc)::value;
-                nb[q] = __ldg(d.vsite + v + d.off[q]);
+                nb[q] = __ldg(d.vsite + v + stencil_off(d, q));
             });
         }
     }
@@ -265,35 +269,37 @@ struct SlotCache {
 // Incoming distributions of site n (voxel v), as deviations d_q = f_q - t_q
 // from the rest state (exact in fp32 near rest), so that density and
 // momentum are sums of small numbers and the relaxation acts on small
-// quantities. Odd steps also fill the slot cache.
+// quantities; in working units, i.e. times S::kK. Odd steps also fill the
+// slot cache.
 template <int PAR, class S>
 __device__ __forceinline__ void load_f(const DomainView& d, int n, int v, float (&f)[Q19], SlotCache sc) {
     const int Ni = d.n_sites;
     const size_t N = static_cast<size_t>(Ni);
     const typename S::T* const F = static_cast<const typename S::T*>(d.f);
+    constexpr float K = S::kK;
     if constexpr (PAR == 0) {
         // even step: own slots, row q; fp16 references are all this site's
         float r = 0.0f;
         if constexpr (S::kRef) r = d.drho[n];
         static_for<0, Q19>([&](auto qc) {
             constexpr int q = decltype(qc)::value;
-            f[q] = S::template ld_fdev<q>(F + q * N + n);
-            if constexpr (S::kRef) f[q] = fmaf(t19(q), r, f[q]);
+            f[q] = S::template ld_fs<q>(F + q * N + n);
+            if constexpr (S::kRef) f[q] = fmaf(t19(q) * K, r, f[q]);
         });
     } else {
-        f[0] = S::template ld_fdev<0>(F + n);
-        if constexpr (S::kRef) f[0] = fmaf(t19(0), d.drho[n], f[0]);
+        f[0] = S::template ld_fs<0>(F + n);
+        if constexpr (S::kRef) f[0] = fmaf(t19(0) * K, d.drho[n], f[0]);
         static_for<1, Q19>([&](auto qc) {
             constexpr int q = decltype(qc)::value;   // direction of the downstream slot
             constexpr int o = opp(q);                // direction read from it
-            const int m = __ldg(d.vsite + v + d.off[q]);
+            const int m = __ldg(d.vsite + v + stencil_off(d, q));
             const int s = m >= 0 ? m : n + (o - q) * Ni;
             sc.slot[(q - 1) * sc.stride] = s;
-            f[o] = S::template ld_fdev<o>(F + q * N + s);
+            f[o] = S::template ld_fs<o>(F + q * N + s);
             if constexpr (S::kRef) {
                 const float r = d.drho[m >= 0 ? m : n];
                 sc.ref[(q - 1) * sc.stride] = r;
-                f[o] = fmaf(t19(o), r, f[o]);
+                f[o] = fmaf(t19(o) * K, r, f[o]);
             }
         });
     }
@@ -360,6 +366,11 @@ __device__ __forceinline__ void collide_site(const DomainView& d, int n, const f
     using T = typename S::T;
     const size_t N = static_cast<size_t>(d.n_sites);
     T* const F = static_cast<T*>(d.f);
+    // f, drho and j are in working units (times K); the equilibrium's
+    // quadratic terms take one factor 1/K, the interfacial terms and the
+    // forcing (d.fterm is stored in working units) one factor K
+    constexpr float K = S::kK;
+    constexpr float iK = 1.0f / K;
     const float drho = mo.drho, jx = mo.jx, jy = mo.jy, jz = mo.jz;
 
     const float C2 = Cx * Cx + Cy * Cy + Cz * Cz;
@@ -393,7 +404,7 @@ __device__ __forceinline__ void collide_site(const DomainView& d, int n, const f
     // m13, m14, m15 (rho0 = 1). Everything below is relative to the rest
     // state t_q (rho = 1), i.e. in deviations.
     const float jj = jx * jx + jy * jy + jz * jz;
-    const float ac = d.alpha * Cmag;
+    const float ac = (d.alpha * K) * Cmag;
     const float hac = 0.5f * ac;
     float dma[Q19];
     dma[1] = -ac;
@@ -402,7 +413,7 @@ __device__ __forceinline__ void collide_site(const DomainView& d, int n, const f
     dma[13] = hac * nx * ny;
     dma[14] = hac * ny * nz;
     dma[15] = hac * nx * nz;
-    const float drho_iso = drho - 1.5f * jj;
+    const float drho_iso = fmaf(-1.5f * iK, jj, drho);
 
     // recoloring weights Nb/N and Na/N are (1 - phi)/2 and (1 + phi)/2
     const float bxa = d.beta * 0.5f * (1.0f - phi_c);
@@ -428,7 +439,7 @@ __device__ __forceinline__ void collide_site(const DomainView& d, int n, const f
         if constexpr (cx(q) != 0) cu += cx(q) * jx;
         if constexpr (cy(q) != 0) cu += cy(q) * jy;
         if constexpr (cz(q) != 0) cu += cz(q) * jz;
-        float eqp = t * fmaf(4.5f * cu, cu, drho_iso);
+        float eqp = t * fmaf((4.5f * iK) * cu, cu, drho_iso);
         static_for<1, 16>([&](auto kc) {
             constexpr int k = decltype(kc)::value;
             if constexpr (k == 1 || k == 9 || k == 11 || k == 13 || k == 14 || k == 15) {
@@ -450,19 +461,22 @@ __device__ __forceinline__ void collide_site(const DomainView& d, int n, const f
                 vq = fmaf(-t, drho, vq);
                 vo = fmaf(-t, drho, vo);
             } else {
-                vq = fmaf(-t, sc.ref[(q - 1) * sc.stride], vq);
-                vo = fmaf(-t, sc.ref[(o - 1) * sc.stride], vo);
+                vq = fmaf(-t * K, sc.ref[(q - 1) * sc.stride], vq);
+                vo = fmaf(-t * K, sc.ref[(o - 1) * sc.stride], vo);
             }
         }
-        S::template st_fdev<q>(dst(std::integral_constant<int, q>{}, F), vq);
-        S::template st_fdev<o>(dst(std::integral_constant<int, o>{}, F), vo);
+        S::template st_fs<q>(dst(std::integral_constant<int, q>{}, F), vq);
+        S::template st_fs<o>(dst(std::integral_constant<int, o>{}, F), vo);
     });
     if constexpr (S::kRef) {
-        const float r0 = PAR == 0 ? drho : d.drho[n];
-        S::template st_fdev<0>(F + n, fmaf(-t19(0), r0, f[0] - dsum));
-        if constexpr (PAR == 0) d.drho[n] = drho;
+        if constexpr (PAR == 0) {
+            S::template st_fs<0>(F + n, fmaf(-t19(0), drho, f[0] - dsum));
+            d.drho[n] = drho * iK;
+        } else {
+            S::template st_fs<0>(F + n, fmaf(-t19(0) * K, d.drho[n], f[0] - dsum));
+        }
     } else {
-        S::template st_fdev<0>(F + n, f[0] - dsum);
+        S::template st_fs<0>(F + n, f[0] - dsum);
     }
 
     // recolored component distributions (Eqs. LBE-mass-a/b), streamed on the
@@ -470,8 +484,10 @@ __device__ __forceinline__ void collide_site(const DomainView& d, int n, const f
     // fp32 weights (whose sum is not exactly 1) create no mass. With fp16
     // storage the stored quantity is the deviation from w_q Na (w_q Nb), which
     // the formula gives directly: w_q Na (4.5 u.xi + beta Nb/N n.xi).
+    // (working units: Na, Nb times K, j divided by K back to u)
     T* const A = static_cast<T*>(d.a);
     T* const B = static_cast<T*>(d.b);
+    const float NaK = Na * K, NbK = Nb * K;
     float asum = 0.0f, bsum = 0.0f;
     static_for<1, Q7>([&](auto qc) {
         constexpr int q = decltype(qc)::value;
@@ -481,25 +497,25 @@ __device__ __forceinline__ void collide_site(const DomainView& d, int n, const f
         if constexpr (cz(q) != 0) { ux = cz(q) * jz; nn = cz(q) * nz; }
         float av, bv;
         if constexpr (S::kRef) {
-            const float du = 4.5f * ux;
-            av = w7(q) * Na * (du + bxa * nn);
-            bv = w7(q) * Nb * (du - bxb * nn);
+            const float du = (4.5f * iK) * ux;
+            av = w7(q) * NaK * (du + bxa * nn);
+            bv = w7(q) * NbK * (du - bxb * nn);
         } else {
-            const float base = 1.0f + 4.5f * ux;
-            av = w7(q) * Na * (base + bxa * nn);
-            bv = w7(q) * Nb * (base - bxb * nn);
+            const float base = fmaf(4.5f * iK, ux, 1.0f);
+            av = w7(q) * NaK * (base + bxa * nn);
+            bv = w7(q) * NbK * (base - bxb * nn);
         }
         asum += av;
         bsum += bv;
-        S::st_c(dst(qc, A), av);
-        S::st_c(dst(qc, B), bv);
+        S::st_cs(dst(qc, A), av);
+        S::st_cs(dst(qc, B), bv);
     });
     if constexpr (S::kRef) {
-        S::st_c(A + n, -asum);
-        S::st_c(B + n, -bsum);
+        S::st_cs(A + n, -asum);
+        S::st_cs(B + n, -bsum);
     } else {
-        S::st_c(A + n, Na - asum);
-        S::st_c(B + n, Nb - bsum);
+        S::st_cs(A + n, NaK - asum);
+        S::st_cs(B + n, NbK - bsum);
     }
 }
 
@@ -520,7 +536,7 @@ __device__ __forceinline__ void collide_thread(const DomainView& d, int n, SlotC
     const float phi_c = *pv;
     float Na, Nb, Cx, Cy, Cz;
     site_nab<PAR, S>(d, n, phi_c, Na, Nb);
-    color_gradient([&](auto qc) { return pv[d.off[decltype(qc)::value]]; }, Cx, Cy, Cz);
+    color_gradient([&](auto qc) { return pv[stencil_off(d, decltype(qc)::value)]; }, Cx, Cy, Cz);
     collide_site<PAR, S>(d, n, f, moments(f), phi_c, Na, Nb, Cx, Cy, Cz, sc);
 }
 
@@ -536,7 +552,7 @@ __device__ __forceinline__ void reservoir_thread(const DomainView& d, int n, int
     if constexpr (PAR == 1 || S::kRef) {
         static_for<1, Q19>([&](auto qc) {
             constexpr int q = decltype(qc)::value;
-            nb[q] = __ldg(d.vsite + v + d.off[q]);
+            nb[q] = __ldg(d.vsite + v + stencil_off(d, q));
         });
     }
     const float rho = side == 1 ? rho_in : rho_out;
