@@ -69,9 +69,10 @@ def kernel_hash(precision: str) -> str:
     return h.hexdigest()[:16]
 
 
-def traffic_per_launch(precision: str, n_sites: int):
-    """DRAM bytes per collide launch from the committed ncu summary, scaled to
-    n_sites; None when the kernel source changed since the capture."""
+def ncu_traffic(precision: str):
+    """DRAM bytes per site of the collide (and, when captured, the phase)
+    kernel from the committed ncu summary; None when the kernel source changed
+    since the capture."""
     p = os.path.join(ROOT, "profiles", "collide_traffic.json")
     if not os.path.exists(p):
         return None
@@ -80,7 +81,13 @@ def traffic_per_launch(precision: str, n_sites: int):
     e = d.get(precision)
     if not e or e.get("kernel_hash") != kernel_hash(precision):
         return None
-    return float(e["bytes_per_site"]) * n_sites
+    return e
+
+
+def traffic_per_launch(precision: str, n_sites: int):
+    """DRAM bytes per collide launch, scaled to n_sites (see ncu_traffic)."""
+    e = ncu_traffic(precision)
+    return None if e is None else float(e["bytes_per_site"]) * n_sites
 
 
 class ClockSampler:
@@ -98,12 +105,18 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
         except (OSError, FileNotFoundError):
             self.proc = None
+
+    def wait_first(self, timeout: float = 3.0):
+        """Block until the first sample arrived, so the timed region is covered."""
+        t0 = time.perf_counter()
+        while self.proc is not None and not self.lines and time.perf_counter() - t0 < timeout:
+            time.sleep(0.01)
 
     def _read(self):
         for line in self.proc.stdout:
@@ -286,6 +299,8 @@ def bench_serving(jobs, precision, lam, seed, max_steps, interval, device, flux_
            "arrival_rate_per_s": lam, "check_interval": interval, "max_steps": max_steps,
            "states": {k: sum(1 for s in st if s["state"] == k) for k in ("done", "failed")},
            "converged_early": sum(1 for s in st if s["steps"] < max_steps),
+           "site_updates": su, "mean_sites": float(np.mean([s["n_sites"] for s in st])),
+           "mean_steps": float(np.mean([s["steps"] for s in st])),
            "kinds": {k: sum(1 for w in jobs if w.meta["kind"] == k) for k in ("steady", "unsteady", "centrifuge")}}
     srv.close()
     return out
@@ -383,6 +398,38 @@ def bench_precision(args):
     return 0
 
 
+SERVING_L = (64, 96, 128, 160, 192, 224, 256, 288, 320, 352, 384)
+
+
+def bench_serving_trace(args):
+    """Serving trace at full size: Poisson arrivals at 20/s of jobs with L in
+    {64, 96, ..., 384}, each stopping on the flux-change test (1e-4 over 500
+    steps) or at 10,000 steps; then the same jobs again at an arrival rate of
+    70 % of the capacity the first run measured, to show the latency of the
+    continuous batcher itself rather than of the queue."""
+    import torch
+    t0 = time.perf_counter()
+    jobs = _spawn_map(_serving_job, [(i, SERVING_L) for i in range(args.serving_jobs)])
+    gen_s = time.perf_counter() - t0
+    torch.cuda.set_device(0)
+    prec = args.precision
+    out = {"metric": "serving latency p50/p99 and aggregate pore-site MLUPS", "unit": "MLUPS",
+           "workload": (f"{len(jobs)} jobs, L uniform on {SERVING_L}, porosity U[0.15, 0.35], 50 % steady, "
+                        f"30 % unsteady, 20 % centrifuge; flux-change 1e-4 every 500 steps or "
+                        f"{args.serving_max_steps} steps; {prec} storage"),
+           "generation_s": gen_s}
+    r1 = bench_serving(jobs, prec, 20.0, 5, args.serving_max_steps, 500, 0)
+    out["lambda_20"] = r1
+    # capacity in jobs per second: aggregate site-update rate over the mean work of a job
+    work = r1["mean_sites"] * r1["mean_steps"]
+    cap = r1["aggregate_value"] * 1e6 / max(work, 1.0)
+    r2 = bench_serving(jobs, prec, 0.7 * cap, 6, args.serving_max_steps, 500, 0)
+    r2["capacity_jobs_per_s"] = cap
+    out["lambda_70pct_capacity"] = r2
+    print(json.dumps(out))
+    return 0
+
+
 def bench_gpu(args):
     import numpy as np
     import torch
@@ -419,6 +466,7 @@ def bench_gpu(args):
     # device-timed region: step bundles replay as CUDA graphs
     sampler = ClockSampler(local_rank)
     sampler.start()
+    sampler.wait_first()
     l0 = dom.launch_count
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
@@ -532,6 +580,15 @@ def bench_gpu(args):
     achieved = bytes_c * N / (c_ms * 1e-3) / 1e9
     traffic = traffic_per_launch(prec, N)
 
+    # HBM fraction the second way: DRAM bytes the ncu capture measured per
+    # site for the collide and phase kernels, over the device-timed step
+    nt = ncu_traffic(prec)
+    step_dram = None
+    if nt is not None and "phase_bytes_per_site" in nt:
+        gbs = (nt["bytes_per_site"] + nt["phase_bytes_per_site"]) * N * bundle * args.steps / (ms * 1e-3) / 1e9
+        step_dram = {"gbs": gbs, "frac": gbs / peak if peak else None, "frac_of_8tbs": gbs / 8000.0,
+                     "bytes_per_site": nt["bytes_per_site"] + nt["phase_bytes_per_site"]}
+
     out = None
     if rank == 0:
         step_gbs = bytes_s * N * bundle * args.steps / (ms * 1e-3) / 1e9
@@ -554,7 +611,7 @@ def bench_gpu(args):
                          "avg_launch_ms": c_ms, "launches": kt["collide_launches"],
                          "phase_avg_launch_ms": p_ms,
                          "step_achieved_gbs": step_gbs, "step_frac": step_gbs / peak,
-                         "step_frac_of_8tbs": step_gbs / 8000.0},
+                         "step_frac_of_8tbs": step_gbs / 8000.0, "step_dram_ncu": step_dram},
             "e2e": {"value": e2e_value, "unit": "MLUPS", "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": 27 * 8, "steps": e2e_steps},
             "fp16": fp16,
@@ -574,6 +631,10 @@ def bench_gpu(args):
                 out["cpu_baseline"] = {"value": cv, "unit": "MLUPS", "cores": threads, "kind": "oracle",
                                        "sample": f"{len(times)} timesteps of the same workload "
                                                  f"({n} sites), OpenMP={oracle.have_openmp()}"}
+                n1, t1 = run_cpu_baseline(w, 3, 1)
+                out["cpu_baseline"]["single_thread"] = {
+                    "value": n1 * len(t1) / sum(t1) / 1e6, "unit": "MLUPS", "cores": 1,
+                    "sample": f"{len(t1)} timesteps of the same workload, one thread"}
             except Exception as exc:  # the baseline is informative only
                 out["cpu_baseline"] = {"value": None, "unit": "MLUPS", "cores": None,
                                        "kind": "oracle", "sample": f"failed: {exc}"}
@@ -591,7 +652,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--mode", default="headline", choices=["headline", "precision"])
+    ap.add_argument("--mode", default="headline", choices=["headline", "precision", "serving"])
     ap.add_argument("--precision-steps", type=int, default=5000)
     ap.add_argument("--crop-steps", type=int, default=5000)
     ap.add_argument("--size", type=int, default=256)
@@ -611,6 +672,8 @@ def main():
         return bench_reference(args)
     if args.mode == "precision":
         return bench_precision(args)
+    if args.mode == "serving":
+        return bench_serving_trace(args)
     return bench_gpu(args)
 
 

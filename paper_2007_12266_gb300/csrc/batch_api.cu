@@ -36,7 +36,7 @@ struct lbpm_batch {
     bool dirty = true;
     // launch shape
     int bt = 256;
-    int bps[2] = {0, 0};   // resident blocks per SM used for the persistent grids (0 = occupancy limit)
+    int bps[2] = {0, 0};   // resident blocks per SM of the persistent grids (0 = occupancy limit, -1 = one block per tile)
     int n_sm = 0;
     // bundle graph (2 timesteps)
     cudaStream_t cap_stream = nullptr;
@@ -159,6 +159,7 @@ lbpm_status rebuild(lbpm_batch* b) {
 }
 
 unsigned grid_for(const lbpm_batch* b, int k) {
+    if (b->bps[k] < 0) return static_cast<unsigned>(std::max(1, b->n_tiles[k]));   // one block per tile
     const int occ = batch_max_blocks(k, b->precision == LBPM_FP16, b->bt);
     const int bps = b->bps[k] > 0 ? std::min(b->bps[k], occ) : occ;
     const long long persistent = static_cast<long long>(bps) * b->n_sm;
@@ -365,7 +366,7 @@ lbpm_status lbpm_batch_set_launch(lbpm_batch* b, int threads, int bps_phase, int
     if (s) return s;
     if (threads != 128 && threads != 256 && threads != 512)
         return bfail(b, LBPM_E_INVALID, "threads per block must be 128, 256 or 512");
-    if (bps_phase < 0 || bps_collide < 0) return bfail(b, LBPM_E_INVALID, "blocks per SM must be >= 0");
+    if (bps_phase < -1 || bps_collide < -1) return bfail(b, LBPM_E_INVALID, "blocks per SM must be >= -1");
     LBPM_BCK(b, cudaStreamSynchronize(b->stream));
     if (threads != b->bt) b->dirty = true;
     b->bt = threads;
@@ -396,8 +397,9 @@ lbpm_status lbpm_batch_tune(lbpm_batch* b, int steps_per_candidate, int* threads
         const bool h = b->precision == LBPM_FP16;
         for (int bt : {128, 256, 512}) {
             const int occ = std::min(batch_max_blocks(0, h, bt), batch_max_blocks(1, h, bt));
-            for (int frac : {4, 2, 1}) {  // occupancy limit, half of it, a quarter
-                const int bps = std::max(1, occ * frac / 4);
+            // one block per tile, then persistent grids at the occupancy limit, half of it, a quarter
+            for (int frac : {-1, 4, 2, 1}) {
+                const int bps = frac < 0 ? -1 : std::max(1, occ * frac / 4);
                 if ((s = lbpm_batch_set_launch(b, bt, bps, bps))) break;
                 if ((s = lbpm_batch_advance(b, 2))) break;  // capture + warm up
                 cudaEventRecord(e0, b->stream);
