@@ -30,57 +30,50 @@ namespace {
 
 constexpr int kMaxBlocksPerSm = 16;
 
-// Blocks walk the tile list round-robin (tile blockIdx.x, then + gridDim.x,
-// ...), so the tiles in flight at any moment are neighbours in the list and
-// their phi stencils and neighbour ids share L2 lines; a block reloads the
-// job's view into shared memory only when its next tile belongs to another
-// job.
-__device__ __forceinline__ void load_view(DomainView& sv, const DomainView* views, int job) {
-    __syncthreads();   // every thread is done with the previous view
-    if (threadIdx.x < static_cast<int>(sizeof(DomainView) / sizeof(int)))
-        reinterpret_cast<int*>(&sv)[threadIdx.x] = reinterpret_cast<const int*>(views + job)[threadIdx.x];
-    __syncthreads();
+// Blocks take tiles blockIdx.x, + gridDim.x, ... (one tile per block when the
+// grid covers them all), so the tiles in flight at any moment are neighbours
+// in the numbering and their phi stencils and neighbour ids share L2 lines.
+static_assert(sizeof(BatchLaunch) <= 32000, "job table must fit the kernel parameter space");
+
+// job owning tile t: the last j with tile_begin[j] <= t (uniform search)
+__device__ __forceinline__ int job_of_tile(const BatchLaunch& p, int t) {
+    int lo = 0, hi = p.n_jobs;   // tile_begin[lo] <= t < tile_begin[hi]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (p.tile_begin[mid] <= t) lo = mid;
+        else hi = mid;
+    }
+    return lo;
 }
 
 template <int PAR, class S, int BT>
-__global__ void __launch_bounds__(BT) k_batch_phase(const DomainView* views, const BatchTile* tiles, int n_tiles) {
-    __shared__ DomainView sv;
-    int job = -1;
-    for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
-        const BatchTile tl = tiles[t];
-        if (tl.job != job) {
-            load_view(sv, views, tl.job);
-            job = tl.job;
-        }
-        phase_thread<PAR, S>(sv, tl.first + threadIdx.x);
+__global__ void __launch_bounds__(BT) k_batch_phase(const __grid_constant__ BatchLaunch p) {
+    const int nt = p.tile_begin[p.n_jobs];
+    for (int t = blockIdx.x; t < nt; t += gridDim.x) {
+        const int j = job_of_tile(p, t);
+        phase_thread<PAR, S>(p.v[j], (t - p.tile_begin[j]) * BT + threadIdx.x);
     }
 }
 
 template <int PAR, class S, int BT>
-__global__ void __launch_bounds__(BT, 1024 / BT) k_batch_collide(const DomainView* views, const BatchTile* tiles, int n_tiles) {
-    __shared__ DomainView sv;
+__global__ void __launch_bounds__(BT, 1024 / BT) k_batch_collide(const __grid_constant__ BatchLaunch p) {
     constexpr int kSlots = PAR == 1 ? (Q19 - 1) * BT : 1;
     constexpr int kRefs = PAR == 1 && S::kRef ? (Q19 - 1) * BT : 1;
     __shared__ int slot[kSlots];
     __shared__ float ref[kRefs];
-    int job = -1;
-    for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
-        const BatchTile tl = tiles[t];
-        if (tl.job != job) {
-            load_view(sv, views, tl.job);
-            job = tl.job;
-        }
-        const int n = tl.first + threadIdx.x;
-        if (n < sv.n_sites) collide_thread<PAR, S>(sv, n, SlotCache{slot + threadIdx.x, ref + threadIdx.x, BT});
+    const int nt = p.tile_begin[p.n_jobs];
+    for (int t = blockIdx.x; t < nt; t += gridDim.x) {
+        const int j = job_of_tile(p, t);
+        const DomainView& d = p.v[j];
+        const int n = (t - p.tile_begin[j]) * BT + threadIdx.x;
+        if (n < d.n_sites) collide_thread<PAR, S>(d, n, SlotCache{slot + threadIdx.x, ref + threadIdx.x, BT});
     }
 }
-
-static_assert(sizeof(DomainView) % sizeof(int) == 0, "view copied as ints");
 
 template <int BT>
 struct Launch {
     template <class K>
-    static cudaError_t go(K kernel, unsigned grid, cudaStream_t s, const DomainView* v, const BatchTile* t, int nt) {
+    static cudaError_t go(K kernel, unsigned grid, cudaStream_t s, const BatchLaunch& p) {
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(grid);
         cfg.blockDim = dim3(BT);
@@ -90,47 +83,47 @@ struct Launch {
         attr[0].val.programmaticStreamSerializationAllowed = 1;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
-        return cudaLaunchKernelEx(&cfg, kernel, v, t, nt);
+        return cudaLaunchKernelEx(&cfg, kernel, p);
     }
 };
 
 template <int BT>
-cudaError_t batch_phase_bt(int par, bool fp16, unsigned grid, cudaStream_t s, const DomainView* v,
-                           const BatchTile* t, int nt) {
+cudaError_t batch_phase_bt(int par, bool fp16, unsigned grid, cudaStream_t s, const BatchLaunch& p) {
     if (par == 0)
-        return fp16 ? Launch<BT>::go(k_batch_phase<0, StoreF16, BT>, grid, s, v, t, nt)
-                    : Launch<BT>::go(k_batch_phase<0, StoreF32, BT>, grid, s, v, t, nt);
-    return fp16 ? Launch<BT>::go(k_batch_phase<1, StoreF16, BT>, grid, s, v, t, nt)
-                : Launch<BT>::go(k_batch_phase<1, StoreF32, BT>, grid, s, v, t, nt);
+        return fp16 ? Launch<BT>::go(k_batch_phase<0, StoreF16, BT>, grid, s, p)
+                    : Launch<BT>::go(k_batch_phase<0, StoreF32, BT>, grid, s, p);
+    return fp16 ? Launch<BT>::go(k_batch_phase<1, StoreF16, BT>, grid, s, p)
+                : Launch<BT>::go(k_batch_phase<1, StoreF32, BT>, grid, s, p);
 }
 
 template <int BT>
-cudaError_t batch_collide_bt(int par, bool fp16, unsigned grid, cudaStream_t s, const DomainView* v,
-                             const BatchTile* t, int nt) {
+cudaError_t batch_collide_bt(int par, bool fp16, unsigned grid, cudaStream_t s, const BatchLaunch& p) {
     if (par == 0)
-        return fp16 ? Launch<BT>::go(k_batch_collide<0, StoreF16, BT>, grid, s, v, t, nt)
-                    : Launch<BT>::go(k_batch_collide<0, StoreF32, BT>, grid, s, v, t, nt);
-    return fp16 ? Launch<BT>::go(k_batch_collide<1, StoreF16, BT>, grid, s, v, t, nt)
-                : Launch<BT>::go(k_batch_collide<1, StoreF32, BT>, grid, s, v, t, nt);
+        return fp16 ? Launch<BT>::go(k_batch_collide<0, StoreF16, BT>, grid, s, p)
+                    : Launch<BT>::go(k_batch_collide<0, StoreF32, BT>, grid, s, p);
+    return fp16 ? Launch<BT>::go(k_batch_collide<1, StoreF16, BT>, grid, s, p)
+                : Launch<BT>::go(k_batch_collide<1, StoreF32, BT>, grid, s, p);
 }
 
 }  // namespace
 
-// Launch one phase (0 = phase pass, 1 = collide-stream) over all tiles.
+// Launch one phase (0 = phase pass, 1 = collide-stream) over the jobs of p.
 cudaError_t launch_batch(int kernel, int par, bool fp16, int bt, unsigned grid, cudaStream_t s,
-                         const DomainView* v, const BatchTile* t, int nt) {
-    if (nt == 0) return cudaSuccess;
+                         const BatchLaunch& p) {
+    if (p.n_jobs == 0 || p.tile_begin[p.n_jobs] == 0) return cudaSuccess;
     switch (bt) {
-    case 128: return kernel == 0 ? batch_phase_bt<128>(par, fp16, grid, s, v, t, nt)
-                                 : batch_collide_bt<128>(par, fp16, grid, s, v, t, nt);
-    case 512: return kernel == 0 ? batch_phase_bt<512>(par, fp16, grid, s, v, t, nt)
-                                 : batch_collide_bt<512>(par, fp16, grid, s, v, t, nt);
-    default: return kernel == 0 ? batch_phase_bt<256>(par, fp16, grid, s, v, t, nt)
-                                : batch_collide_bt<256>(par, fp16, grid, s, v, t, nt);
+    case 128: return kernel == 0 ? batch_phase_bt<128>(par, fp16, grid, s, p)
+                                 : batch_collide_bt<128>(par, fp16, grid, s, p);
+    case 512: return kernel == 0 ? batch_phase_bt<512>(par, fp16, grid, s, p)
+                                 : batch_collide_bt<512>(par, fp16, grid, s, p);
+    default: return kernel == 0 ? batch_phase_bt<256>(par, fp16, grid, s, p)
+                                : batch_collide_bt<256>(par, fp16, grid, s, p);
     }
 }
 
 namespace {
+
+static_assert(sizeof(DomainView) % sizeof(int) == 0, "view copied as ints");
 
 // Per-tile fp64 partial sums of the measures; each job's parity is read per tile.
 template <class S, int BT>

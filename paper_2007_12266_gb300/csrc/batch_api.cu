@@ -25,13 +25,12 @@ struct lbpm_batch {
     // device tables
     DomainView* d_views = nullptr;
     int* d_parity = nullptr;
-    BatchTile* d_tiles[2] = {nullptr, nullptr};  // phase, collide (tile = bt threads)
+    std::vector<BatchLaunch> launch[2];          // phase, collide job tables (tile = bt threads)
     BatchTile* d_mtiles = nullptr;               // measure tiles (256 sites)
     int* d_mbegin = nullptr;                     // [J+1] first measure tile of each job
     double* d_partials = nullptr;
     double* d_out = nullptr;
-    size_t cap_views = 0, cap_tiles[2] = {0, 0}, cap_mtiles = 0;
-    int n_tiles[2] = {0, 0};
+    size_t cap_views = 0, cap_mtiles = 0;
     int n_mtiles = 0;
     bool dirty = true;
     // launch shape
@@ -107,16 +106,27 @@ lbpm_status rebuild(lbpm_batch* b) {
     const int J = static_cast<int>(b->jobs.size());
     std::vector<DomainView> views(J);
     std::vector<int> parity(J);
-    std::vector<BatchTile> tiles[2];
     std::vector<BatchTile> mtiles;
     std::vector<int> mbegin(J + 1, 0);
+    for (int k = 0; k < 2; ++k) b->launch[k].clear();
     for (int j = 0; j < J; ++j) {
         const lbpm_ctx* c = b->jobs[j];
         views[j] = make_view(c);
         parity[j] = static_cast<int>(c->step & 1);
         const long long counts[2] = {c->N + c->H, c->N};
-        for (int k = 0; k < 2; ++k)
-            for (long long f = 0; f < counts[k]; f += b->bt) tiles[k].push_back(BatchTile{j, static_cast<int>(f)});
+        for (int k = 0; k < 2; ++k) {
+            if (j % kBatchLaunchJobs == 0) {
+                b->launch[k].emplace_back();
+                std::memset(&b->launch[k].back(), 0, sizeof(BatchLaunch));
+            }
+            BatchLaunch& L = b->launch[k].back();
+            const long long tiles = (counts[k] + b->bt - 1) / b->bt;
+            if (L.tile_begin[L.n_jobs] + tiles > (1LL << 30))
+                return bfail(b, LBPM_E_INVALID, "batch too large for one launch table");
+            L.v[L.n_jobs] = views[j];
+            L.tile_begin[L.n_jobs + 1] = L.tile_begin[L.n_jobs] + static_cast<int>(tiles);
+            ++L.n_jobs;
+        }
         mbegin[j] = static_cast<int>(mtiles.size());
         for (long long f = 0; f < c->N; f += 256) mtiles.push_back(BatchTile{j, static_cast<int>(f)});
     }
@@ -133,9 +143,6 @@ lbpm_status rebuild(lbpm_batch* b) {
     b->d_out = static_cast<double*>(balloc(b, sizeof(double) * NSUM * std::max(J, 1)));
     if (!b->d_parity || !b->d_mbegin || !b->d_partials || !b->d_out)
         return bfail(b, LBPM_E_OOM, "batch table allocation failed");
-    for (int k = 0; k < 2; ++k)
-        if (!ensure(b, &b->d_tiles[k], &b->cap_tiles[k], tiles[k].size()))
-            return bfail(b, LBPM_E_OOM, "batch tile allocation failed");
     if (!ensure(b, &b->d_mtiles, &b->cap_mtiles, mtiles.size()))
         return bfail(b, LBPM_E_OOM, "batch tile allocation failed");
     if (J) {
@@ -143,12 +150,6 @@ lbpm_status rebuild(lbpm_batch* b) {
         LBPM_BCK(b, cudaMemcpyAsync(b->d_parity, parity.data(), sizeof(int) * J, cudaMemcpyHostToDevice, b->stream));
     }
     LBPM_BCK(b, cudaMemcpyAsync(b->d_mbegin, mbegin.data(), sizeof(int) * (J + 1), cudaMemcpyHostToDevice, b->stream));
-    for (int k = 0; k < 2; ++k) {
-        b->n_tiles[k] = static_cast<int>(tiles[k].size());
-        if (b->n_tiles[k])
-            LBPM_BCK(b, cudaMemcpyAsync(b->d_tiles[k], tiles[k].data(), sizeof(BatchTile) * tiles[k].size(),
-                                        cudaMemcpyHostToDevice, b->stream));
-    }
     b->n_mtiles = static_cast<int>(mtiles.size());
     if (b->n_mtiles)
         LBPM_BCK(b, cudaMemcpyAsync(b->d_mtiles, mtiles.data(), sizeof(BatchTile) * mtiles.size(),
@@ -158,19 +159,22 @@ lbpm_status rebuild(lbpm_batch* b) {
     return LBPM_OK;
 }
 
-unsigned grid_for(const lbpm_batch* b, int k) {
-    if (b->bps[k] < 0) return static_cast<unsigned>(std::max(1, b->n_tiles[k]));   // one block per tile
+unsigned grid_for(const lbpm_batch* b, int k, const BatchLaunch& L) {
+    const int n_tiles = L.tile_begin[L.n_jobs];
+    if (b->bps[k] < 0) return static_cast<unsigned>(std::max(1, n_tiles));   // one block per tile
     const int occ = batch_max_blocks(k, b->precision == LBPM_FP16, b->bt);
     const int bps = b->bps[k] > 0 ? std::min(b->bps[k], occ) : occ;
     const long long persistent = static_cast<long long>(bps) * b->n_sm;
-    return static_cast<unsigned>(std::max<long long>(1, std::min<long long>(persistent, b->n_tiles[k])));
+    return static_cast<unsigned>(std::max<long long>(1, std::min<long long>(persistent, n_tiles)));
 }
 
 cudaError_t enqueue_step(lbpm_batch* b, int par, cudaStream_t s) {
     const bool h = b->precision == LBPM_FP16;
-    cudaError_t e = launch_batch(0, par, h, b->bt, grid_for(b, 0), s, b->d_views, b->d_tiles[0], b->n_tiles[0]);
-    if (e == cudaSuccess)
-        e = launch_batch(1, par, h, b->bt, grid_for(b, 1), s, b->d_views, b->d_tiles[1], b->n_tiles[1]);
+    cudaError_t e = cudaSuccess;
+    for (size_t i = 0; i < b->launch[0].size() && e == cudaSuccess; ++i) {
+        e = launch_batch(0, par, h, b->bt, grid_for(b, 0, b->launch[0][i]), s, b->launch[0][i]);
+        if (e == cudaSuccess) e = launch_batch(1, par, h, b->bt, grid_for(b, 1, b->launch[1][i]), s, b->launch[1][i]);
+    }
     for (lbpm_ctx* c : b->jobs)
         if (e == cudaSuccess && c->n_slab) e = launch_reservoir(c, par ^ 1, s);
     return e;
@@ -192,7 +196,7 @@ lbpm_status capture(lbpm_batch* b) {
 }
 
 int kernels_per_bundle(const lbpm_batch* b) {
-    int k = 4;
+    int k = 4 * static_cast<int>(b->launch[0].size());
     for (const lbpm_ctx* c : b->jobs) k += c->n_slab ? 2 : 0;
     return k;
 }
@@ -242,8 +246,6 @@ lbpm_status lbpm_batch_destroy(lbpm_batch* b) {
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
     bfree(b, b->d_views);
     bfree(b, b->d_parity);
-    bfree(b, b->d_tiles[0]);
-    bfree(b, b->d_tiles[1]);
     bfree(b, b->d_mtiles);
     bfree(b, b->d_mbegin);
     bfree(b, b->d_partials);

@@ -136,8 +136,20 @@ struct BatchTile {
     int job;
     int first;
 };
+// Job table of one batched step launch, passed by value in the kernel's
+// parameter space (at most kBatchLaunchJobs jobs per launch; larger batches
+// take several launches per kernel). Tiles of bt threads are numbered job by
+// job: job j owns tiles [tile_begin[j], tile_begin[j + 1]). Every thread of a
+// block finds its job from blockIdx alone, so the job index and the view's
+// fields are warp-uniform values read from the constant bank.
+constexpr int kBatchLaunchJobs = 128;
+struct BatchLaunch {
+    int n_jobs;
+    int tile_begin[kBatchLaunchJobs + 1];
+    DomainView v[kBatchLaunchJobs];
+};
 cudaError_t launch_batch(int kernel, int par, bool fp16, int bt, unsigned grid, cudaStream_t s,
-                         const DomainView* v, const BatchTile* t, int nt);
+                         const BatchLaunch& p);
 cudaError_t launch_batch_measure(bool fp16, unsigned grid, cudaStream_t s, const DomainView* v, const int* parity,
                                  const BatchTile* t, int nt, double* partials, const int* tile_begin, int n_jobs,
                                  double* out);
