@@ -350,6 +350,14 @@ typedef struct {
     double flux_tol;
     double sw_tol;
     double force_factor, force_cap;
+    /* Steady-state jobs: body-force adaptation to a target capillary number
+     * (Sec. 4.2, Eq. LB_body_force_adaptation). ca_target > 0 rescales the
+     * force by lbpm_force_rescale every relax_steps steps (rounded up to the
+     * check interval) while |Ca / ca_target - 1| >= ca_tol, and the job can
+     * only converge once Ca is within ca_tol of the target. 0 = off. */
+    double ca_target;
+    long long relax_steps;
+    double ca_tol;
 } lbpm_job_spec;
 
 /* Job status; times in seconds on the server's steady clock. */
@@ -359,8 +367,9 @@ typedef struct {
     long long n_sites;
     size_t footprint;
     double t_submit, t_admit, t_done;
-    int force_raises;
+    int force_raises;      /* centrifuge raises or capillary-number rescales so far */
     lbpm_measures last;
+    double force[3];       /* body force in effect */
 } lbpm_job_status;
 
 /* hbm_budget_bytes = 0: 90 % of the free device memory. check_interval:
@@ -381,6 +390,15 @@ lbpm_status lbpm_server_cancel(lbpm_server* server, long long ticket);
 lbpm_status lbpm_server_release(lbpm_server* server, long long ticket);
 lbpm_status lbpm_server_stats(const lbpm_server* server, long long* site_updates, size_t* used_bytes,
                               size_t* budget_bytes);
+
+/* Body-force adaptation to a target capillary number (Sec. 4.2, Eq.
+ * LB_body_force_adaptation): out = g * force with g = ca_target / ca clamped
+ * to [1 / max_factor, max_factor] (the paper caps each change at a factor of
+ * two: max_factor = 2). ca <= 0 (no flow yet) gives g = max_factor. Host
+ * arithmetic only. *factor (may be NULL) receives g. Errors: LBPM_E_INVALID
+ * for NULL force/out, ca_target <= 0, max_factor < 1 or a non-finite input. */
+lbpm_status lbpm_force_rescale(const double force[3], double ca, double ca_target, double max_factor,
+                               double out[3], double* factor);
 
 /* Number of kernel launches issued by this ctx since creation. */
 lbpm_status lbpm_launch_count(const lbpm_ctx* ctx, long long* launches);

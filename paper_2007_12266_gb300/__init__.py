@@ -22,7 +22,8 @@ import numpy as np
 from . import _lib
 from ._lib import JobSpec, JobStatus, LBPMError, Measures, Params
 
-__all__ = ["Domain", "Batch", "Server", "JOB_KINDS", "JOB_STATES", "LBPMError", "FIELDS", "DISTS", "library_path", "version"]
+__all__ = ["Domain", "Batch", "Server", "JOB_KINDS", "JOB_STATES", "LBPMError", "FIELDS", "DISTS", "library_path",
+           "version", "force_rescale"]
 
 FIELDS = {"phi": 0, "pressure": 1, "ux": 2, "uy": 3, "uz": 4, "na": 5, "nb": 6, "rho": 7}
 DISTS = {"f": (0, 19), "a": (1, 7), "b": (2, 7)}
@@ -37,6 +38,19 @@ def library_path() -> str:
 
 def version() -> str:
     return _lib.load().lbpm_version().decode()
+
+
+def force_rescale(force, ca: float, ca_target: float, max_factor: float = 2.0):
+    """Body force rescaled toward a target capillary number (library call
+    lbpm_force_rescale): returns (new_force, factor)."""
+    L = _lib.load()
+    f = (ct.c_double * 3)(*[float(x) for x in force])
+    out = (ct.c_double * 3)()
+    g = ct.c_double()
+    st = L.lbpm_force_rescale(f, float(ca), float(ca_target), float(max_factor), out, ct.byref(g))
+    if st != 0:
+        raise LBPMError(st, "invalid force rescale arguments")
+    return tuple(out), g.value
 
 
 _LIVE = weakref.WeakSet()
@@ -426,7 +440,7 @@ class Server:
     def submit(self, labels, phi0, affinity=None, *, kind="steady", max_steps=10000, flux_tol=1e-4,
                sw_tol=1e-4, force_factor=2.0, force_cap=1.6e-4, tau_a=0.7, tau_b=0.7, alpha=0.005,
                beta=0.95, force=(0.0, 0.0, 0.0), precision="fp32", periodic=(1, 1, 1), reservoir_z=0,
-               rho_in=1.0, rho_out=1.0) -> int:
+               rho_in=1.0, rho_out=1.0, ca_target=0.0, relax_steps=0, ca_tol=0.05) -> int:
         lab = np.ascontiguousarray(labels, dtype=np.uint16)
         ph = np.ascontiguousarray(phi0, dtype=np.float32)
         aff = None if affinity is None else np.ascontiguousarray(affinity, dtype=np.float32)
@@ -440,6 +454,7 @@ class Server:
         sp.max_steps = int(max_steps)
         sp.flux_tol, sp.sw_tol = float(flux_tol), float(sw_tol)
         sp.force_factor, sp.force_cap = float(force_factor), float(force_cap)
+        sp.ca_target, sp.relax_steps, sp.ca_tol = float(ca_target), int(relax_steps), float(ca_tol)
         t = ct.c_longlong()
         self._check(self._L.lbpm_server_submit(self._h, ct.byref(sp), ct.byref(t)))
         self._shapes[t.value] = lab.shape
@@ -455,7 +470,8 @@ class Server:
         self._check(self._L.lbpm_server_poll(self._h, int(ticket), ct.byref(st)))
         return {"state": JOB_STATES[st.state], "steps": st.steps, "n_sites": st.n_sites,
                 "footprint": st.footprint, "t_submit": st.t_submit, "t_admit": st.t_admit,
-                "t_done": st.t_done, "force_raises": st.force_raises, "last": _measures_dict(st.last)}
+                "t_done": st.t_done, "force_raises": st.force_raises, "last": _measures_dict(st.last),
+                "force": tuple(st.force)}
 
     def job(self, ticket: int) -> _JobView:
         h = ct.c_void_p()

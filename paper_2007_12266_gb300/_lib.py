@@ -51,6 +51,7 @@ class JobSpec(ct.Structure):
         ("max_steps", ct.c_longlong),
         ("flux_tol", ct.c_double), ("sw_tol", ct.c_double),
         ("force_factor", ct.c_double), ("force_cap", ct.c_double),
+        ("ca_target", ct.c_double), ("relax_steps", ct.c_longlong), ("ca_tol", ct.c_double),
     ]
 
 
@@ -61,6 +62,7 @@ class JobStatus(ct.Structure):
         ("t_submit", ct.c_double), ("t_admit", ct.c_double), ("t_done", ct.c_double),
         ("force_raises", ct.c_int),
         ("last", Measures),
+        ("force", ct.c_double * 3),
     ]
 
 
@@ -98,6 +100,8 @@ SIGNATURES = {
     "lbpm_kernel_timing": (ct.c_int, [c_ctx_p, ct.POINTER(ct.c_double), ct.POINTER(ct.c_longlong),
                                       ct.POINTER(ct.c_double), ct.POINTER(ct.c_longlong)]),
     "lbpm_launch_count": (ct.c_int, [c_ctx_p, ct.POINTER(ct.c_longlong)]),
+    "lbpm_force_rescale": (ct.c_int, [ct.POINTER(ct.c_double), ct.c_double, ct.c_double, ct.c_double,
+                                      ct.POINTER(ct.c_double), ct.POINTER(ct.c_double)]),
     "lbpm_batch_create": (ct.c_int, [ct.POINTER(ct.c_void_p), ct.c_int, ct.c_void_p]),
     "lbpm_batch_destroy": (ct.c_int, [ct.c_void_p]),
     "lbpm_batch_set_allocator": (ct.c_int, [ct.c_void_p, ALLOC_FN, FREE_FN, ct.c_void_p]),

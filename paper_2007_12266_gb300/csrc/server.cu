@@ -35,6 +35,9 @@
 
 namespace {
 
+// The paper caps each body-force rescale at a factor of two (Sec. 4.2).
+constexpr double kMaxForceRescale = 2.0;
+
 double now_s() {
     using clk = std::chrono::steady_clock;
     static const clk::time_point t0 = clk::now();
@@ -55,6 +58,7 @@ struct Job {
     double q_prev = 0, sw_prev = 0;
     bool have_prev = false;
     int force_raises = 0;
+    long long since_rescale = 0;
     lbpm_measures last{};
     std::string note;
 };
@@ -135,6 +139,20 @@ double driving_flux(const Job* j, const lbpm_measures& m) {
 
 extern "C" {
 
+lbpm_status lbpm_force_rescale(const double force[3], double ca, double ca_target, double max_factor,
+                               double out[3], double* factor) {
+    if (!force || !out || !(ca_target > 0.0) || !(max_factor >= 1.0) || !std::isfinite(ca) ||
+        !std::isfinite(ca_target) || !std::isfinite(max_factor))
+        return LBPM_E_INVALID;
+    for (int a = 0; a < 3; ++a)
+        if (!std::isfinite(force[a])) return LBPM_E_INVALID;
+    // F <- (Ca* / Ca) F, never changed by more than max_factor either way
+    const double g = ca > 0.0 ? std::min(max_factor, std::max(1.0 / max_factor, ca_target / ca)) : max_factor;
+    for (int a = 0; a < 3; ++a) out[a] = g * force[a];
+    if (factor) *factor = g;
+    return LBPM_OK;
+}
+
 lbpm_status lbpm_server_create(lbpm_server** out, int device, void* cuda_stream, size_t hbm_budget_bytes,
                                int max_jobs, int check_interval) {
     if (!out) return LBPM_E_INVALID;
@@ -195,6 +213,11 @@ lbpm_status lbpm_server_submit(lbpm_server* s, const lbpm_job_spec* spec, long l
     if (spec->max_steps < 0 || !(spec->flux_tol > 0.0)) return sfail(s, LBPM_E_INVALID, "bad convergence settings");
     if (spec->kind == LBPM_JOB_CENTRIFUGE && !(spec->force_factor > 1.0))
         return sfail(s, LBPM_E_INVALID, "centrifuge jobs need force_factor > 1");
+    if (spec->ca_target < 0.0 || !std::isfinite(spec->ca_target) || spec->relax_steps < 0 ||
+        (spec->ca_target > 0.0 && !(spec->ca_tol > 0.0)))
+        return sfail(s, LBPM_E_INVALID, "bad capillary-number target settings");
+    if (spec->ca_target > 0.0 && spec->kind != LBPM_JOB_STEADY)
+        return sfail(s, LBPM_E_INVALID, "a capillary-number target applies to steady-state jobs");
     auto j = std::make_unique<Job>();
     j->ticket = s->next_ticket++;
     j->spec = *spec;
@@ -281,7 +304,26 @@ lbpm_status lbpm_server_run(lbpm_server* s, int* n_running, int* n_queued, int* 
                         ramped = true;
                     }
                 }
-                if (!ramped && j->have_prev && std::fabs(q) > 0.0 &&
+                // body-force adaptation to the target capillary number
+                bool on_target = true;
+                j->since_rescale += s->interval;
+                if (j->spec.ca_target > 0.0) {
+                    on_target = std::fabs(m[k].ca / j->spec.ca_target - 1.0) < j->spec.ca_tol;
+                    if (!on_target && j->since_rescale >= j->spec.relax_steps) {
+                        double* F = j->spec.params.force;
+                        double Fn[3];
+                        if (lbpm_force_rescale(F, m[k].ca, j->spec.ca_target, kMaxForceRescale, Fn, nullptr) ==
+                            LBPM_OK) {
+                            for (int a = 0; a < 3; ++a) F[a] = Fn[a];
+                            lbpm_set_params(j->ctx, &j->spec.params);
+                            j->force_raises += 1;
+                            j->since_rescale = 0;
+                            params_changed = true;
+                            ramped = true;
+                        }
+                    }
+                }
+                if (!ramped && on_target && j->have_prev && std::fabs(q) > 0.0 &&
                     std::fabs(q - j->q_prev) / std::fabs(q) < j->spec.flux_tol) {
                     j->state = LBPM_JOB_DONE;
                     j->note = "converged";
@@ -327,6 +369,7 @@ lbpm_status lbpm_server_poll(lbpm_server* s, long long ticket, lbpm_job_status* 
     out->t_admit = j->t_admit;
     out->t_done = j->t_done;
     out->force_raises = j->force_raises;
+    for (int a = 0; a < 3; ++a) out->force[a] = j->spec.params.force[a];
     out->last = j->last;
     return LBPM_OK;
 }

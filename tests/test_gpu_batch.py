@@ -124,6 +124,40 @@ def test_launch_shapes_give_identical_results(precision):
             assert np.array_equal(a, o)
 
 
+def test_more_jobs_than_one_launch_table():
+    """A batch larger than one launch's job table (128 jobs) runs as several
+    launches per kernel; every job still matches its own run."""
+    import paper_2007_12266_gb300 as lbm
+    rng = np.random.default_rng(9)
+    jobs = []
+    for j in range(131):
+        L = (6 + j % 3, 7, 5 + j % 4)
+        lab = np.where(rng.uniform(size=L[::-1]) < 0.2, 1, 0).astype(np.uint16)
+        aff = uniform_affinity(lab, -0.3)
+        phi0 = phi0_iid(lab, 0.5, 300 + j)
+        jobs.append((lab, aff, phi0))
+    kw = dict(periodic=(1, 1, 1), tau_a=0.7, tau_b=0.7, alpha=0.005, beta=0.95, force=(0, 0, 1e-5))
+    doms, alone = [], []
+    for lab, aff, phi0 in jobs:
+        for lst in (doms, alone):
+            d = lbm.Domain(lab, aff, **kw)
+            d.init_fluids(phi0)
+            lst.append(d)
+    b = lbm.Batch()
+    for d in doms:
+        b.add(d)
+    b.set_launch(256, -1, -1)
+    b.advance(6)
+    for da, db in zip(alone, doms):
+        da.advance(6)
+        ga, gb = da.distributions("f").astype(np.float64), db.distributions("f").astype(np.float64)
+        err = np.abs(ga - gb) / np.maximum(np.abs(ga), T19[:, None])
+        assert err.max() <= 1e-5
+    b.close()
+    for d in doms + alone:
+        d.close()
+
+
 def test_batch_rejects_bad_jobs():
     import paper_2007_12266_gb300 as lbm
     specs = _jobs()

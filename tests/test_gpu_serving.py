@@ -114,3 +114,41 @@ def test_admission_by_memory_budget_and_cancel():
         s.release(t)
     assert s.stats()["used_bytes"] == 0
     s.close()
+
+
+def test_body_force_adapts_to_a_target_capillary_number():
+    """Steady-state jobs with a capillary-number target rescale the body force
+    (F <- Ca*/Ca F, at most a factor of two per rescale, every relax_steps)."""
+    import paper_2007_12266_gb300 as lbm
+    spec = _job("steady", 0)
+    F0 = spec["force"][2]
+    probe = lbm.Server(max_jobs=2, check_interval=20)
+    t = probe.submit(**spec, max_steps=200, flux_tol=1e-12)
+    for _ in range(100):
+        if probe.run()[0] == 0:
+            break
+    ca0 = probe.poll(t)["last"]["ca"]
+    probe.close()
+    assert ca0 > 0.0
+    s = lbm.Server(max_jobs=2, check_interval=20)
+    # at most four rescales in 1,200 steps: the force stays small enough to be stable
+    up = s.submit(**spec, max_steps=1200, flux_tol=1e-12, ca_target=3.0 * ca0, relax_steps=300, ca_tol=0.05)
+    # reaches step 200, where its Ca is ca0 exactly (same job, same kernels), then stops
+    same = s.submit(**spec, max_steps=200, flux_tol=1e-12, ca_target=ca0, relax_steps=200, ca_tol=0.01)
+    for _ in range(500):
+        if s.run()[0] == 0:
+            break
+    else:
+        raise AssertionError("jobs did not finish")
+    su, ss = s.poll(up), s.poll(same)
+    assert su["state"] == "done" and ss["state"] == "done"
+    # a target far above the current Ca raised the force, each time by at most 2x
+    assert 1 <= su["force_raises"] <= 4
+    ratio = su["force"][2] / F0
+    assert 1.0 < ratio <= 2.0 ** su["force_raises"] * (1 + 1e-12)
+    assert su["force"][0] == 0.0 and su["force"][1] == 0.0
+    # Ca follows the force upward
+    assert su["last"]["ca"] > ca0
+    # a target already met within its tolerance leaves the force alone
+    assert ss["force_raises"] == 0 and ss["force"][2] == F0
+    s.close()
