@@ -400,6 +400,34 @@ lbpm_status lbpm_server_stats(const lbpm_server* server, long long* site_updates
 lbpm_status lbpm_force_rescale(const double force[3], double ca, double ca_target, double max_factor,
                                double out[3], double* factor);
 
+/* ------------------------------------------------------------------------
+ * Image preparation (Sec. 4.2 mixing region; Sec. 3.3 mixed-wet relabel).
+ * Both run CUDA kernels on `device` on a copy of the caller's host image,
+ * through cudaMalloc/cudaFree and the legacy default stream (they synchronise
+ * before returning), and write the result back into the caller's buffer.
+ * Voxel arrays are x-fastest, nx*ny*nz entries. Errors: LBPM_E_INVALID (NULL
+ * buffer, bad sizes or arguments), LBPM_E_OOM, LBPM_E_CUDA; the host image is
+ * unchanged on error.
+ * ------------------------------------------------------------------------ */
+
+/* Mixing region at the two faces of `axis` (0 = x, 1 = y, 2 = z), n_mix
+ * voxel layers deep (Sec. 4.2): a solid voxel in the first n_mix layers
+ * becomes pore (label 0) where the voxel on the same line in the last layer
+ * (the outlet face) is pore, and a solid voxel in the last n_mix layers
+ * becomes pore where the voxel on its line in the first layer (the inlet
+ * face) is pore. Other voxels keep their labels. 1 <= n_mix <= extent / 2. */
+lbpm_status lbpm_mixing_layer(int device, uint16_t* labels, int nx, int ny, int nz, int axis, int n_mix);
+
+/* Mixed-wet relabel (Sec. 3.3): every solid voxel (label != 0) whose centre
+ * lies within Euclidean distance `radius` of the centre of an oil voxel
+ * (oil[v] != 0) gets label new_label; distances wrap on the periodic axes.
+ * The paper computes a distance transform of the oil phase and relabels the
+ * solid within 2 voxel units; only "distance <= radius" matters, so the kernel
+ * tests the voxel offsets of that ball (33 offsets besides the centre at
+ * radius 2). 0 < radius <= 8, new_label >= 1. */
+lbpm_status lbpm_mixed_wet_relabel(int device, uint16_t* labels, const uint8_t* oil, int nx, int ny, int nz,
+                                   const int periodic[3], double radius, int new_label);
+
 /* Number of kernel launches issued by this ctx since creation. */
 lbpm_status lbpm_launch_count(const lbpm_ctx* ctx, long long* launches);
 

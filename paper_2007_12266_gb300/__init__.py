@@ -23,7 +23,7 @@ from . import _lib
 from ._lib import JobSpec, JobStatus, LBPMError, Measures, Params
 
 __all__ = ["Domain", "Batch", "Server", "JOB_KINDS", "JOB_STATES", "LBPMError", "FIELDS", "DISTS", "library_path",
-           "version", "force_rescale"]
+           "version", "force_rescale", "mixing_layer", "mixed_wet_relabel"]
 
 FIELDS = {"phi": 0, "pressure": 1, "ux": 2, "uy": 3, "uz": 4, "na": 5, "nb": 6, "rho": 7}
 DISTS = {"f": (0, 19), "a": (1, 7), "b": (2, 7)}
@@ -107,6 +107,37 @@ def _torch():
     if not torch.cuda.is_available():
         raise RuntimeError("no CUDA device: the color-LBM library runs on the GPU only")
     return torch
+
+
+def mixing_layer(labels: np.ndarray, n_mix: int, axis: int = 2, device: int = 0) -> np.ndarray:
+    """Mixing region at the inlet/outlet faces of `axis` (library call
+    lbpm_mixing_layer, runs on the GPU). labels: (nz, ny, nx); axis counts
+    x = 0, y = 1, z = 2. Returns the new label image."""
+    _torch()
+    lab = np.array(labels, dtype=np.uint16, order="C", copy=True)
+    nz, ny, nx = lab.shape
+    st = _lib.load().lbpm_mixing_layer(int(device), lab.ctypes.data, nx, ny, nz, int(axis), int(n_mix))
+    if st != 0:
+        raise LBPMError(st, "lbpm_mixing_layer failed")
+    return lab
+
+
+def mixed_wet_relabel(labels: np.ndarray, oil: np.ndarray, radius: float = 2.0, new_label: int = 2,
+                      periodic=(1, 1, 1), device: int = 0) -> np.ndarray:
+    """Relabel the solid within `radius` voxels of the oil phase (library call
+    lbpm_mixed_wet_relabel, runs on the GPU). oil: boolean (nz, ny, nx)."""
+    _torch()
+    lab = np.array(labels, dtype=np.uint16, order="C", copy=True)
+    o = np.ascontiguousarray(oil, dtype=np.uint8)
+    if o.shape != lab.shape:
+        raise ValueError("oil mask must match the image shape")
+    nz, ny, nx = lab.shape
+    per = (ct.c_int * 3)(*[int(p) for p in periodic])
+    st = _lib.load().lbpm_mixed_wet_relabel(int(device), lab.ctypes.data, o.ctypes.data, nx, ny, nz, per,
+                                           float(radius), int(new_label))
+    if st != 0:
+        raise LBPMError(st, "lbpm_mixed_wet_relabel failed")
+    return lab
 
 
 class Domain:

@@ -102,6 +102,9 @@ SIGNATURES = {
     "lbpm_launch_count": (ct.c_int, [c_ctx_p, ct.POINTER(ct.c_longlong)]),
     "lbpm_force_rescale": (ct.c_int, [ct.POINTER(ct.c_double), ct.c_double, ct.c_double, ct.c_double,
                                       ct.POINTER(ct.c_double), ct.POINTER(ct.c_double)]),
+    "lbpm_mixing_layer": (ct.c_int, [ct.c_int, ct.c_void_p, ct.c_int, ct.c_int, ct.c_int, ct.c_int, ct.c_int]),
+    "lbpm_mixed_wet_relabel": (ct.c_int, [ct.c_int, ct.c_void_p, ct.c_void_p, ct.c_int, ct.c_int, ct.c_int,
+                                          ct.POINTER(ct.c_int), ct.c_double, ct.c_int]),
     "lbpm_batch_create": (ct.c_int, [ct.POINTER(ct.c_void_p), ct.c_int, ct.c_void_p]),
     "lbpm_batch_destroy": (ct.c_int, [ct.c_void_p]),
     "lbpm_batch_set_allocator": (ct.c_int, [ct.c_void_p, ALLOC_FN, FREE_FN, ct.c_void_p]),
