@@ -398,6 +398,41 @@ def bench_precision(args):
     return 0
 
 
+def bench_prepare(args):
+    """Image preparation calls on a size^3 sphere pack: mixing region (Sec.
+    4.2) and mixed-wet relabel at radius 2 (Sec. 3.3). Each call copies the
+    image to the device, runs one kernel and copies it back; the line reports
+    the wall time per call (median of 5) and the voxel rate. The kernels'
+    own device times come from the ncu summary in profiles/."""
+    import numpy as np
+    import torch
+
+    import paper_2007_12266_gb300 as lbm
+    from synthetic import phi0_blob, sphere_pack
+    L = args.size
+    t0 = time.perf_counter()
+    lab = sphere_pack(L, 0.2, 10.0, 3.0, 4).labels
+    oil = (phi0_blob(lab, 0.5, 5) < 0) & (lab == 0)
+    gen_s = time.perf_counter() - t0
+    torch.cuda.init()
+    V = lab.size
+    out = {"metric": "image preparation, voxels per second through the C ABI (host copies included)",
+           "unit": "Gvox/s", "workload": f"{L}^3 sphere pack, porosity 0.2, blob oil phase (Sw 0.5)",
+           "voxels": V, "generation_s": gen_s}
+    for name, fn in (("mixing_layer", lambda: lbm.mixing_layer(lab, 8, axis=2)),
+                     ("mixed_wet_relabel", lambda: lbm.mixed_wet_relabel(lab, oil, radius=2.0, new_label=2))):
+        fn()
+        ts = []
+        for _ in range(5):
+            t1 = time.perf_counter()
+            r = fn()
+            ts.append(time.perf_counter() - t1)
+        med = statistics.median(ts)
+        out[name] = {"seconds_per_call": med, "value": V / med / 1e9, "changed_voxels": int(np.count_nonzero(r != lab))}
+    print(json.dumps(out))
+    return 0
+
+
 SERVING_L = (64, 96, 128, 160, 192, 224, 256, 288, 320, 352, 384)
 
 
@@ -652,7 +687,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--mode", default="headline", choices=["headline", "precision", "serving"])
+    ap.add_argument("--mode", default="headline", choices=["headline", "precision", "serving", "prepare"])
     ap.add_argument("--precision-steps", type=int, default=5000)
     ap.add_argument("--crop-steps", type=int, default=5000)
     ap.add_argument("--size", type=int, default=256)
@@ -674,6 +709,8 @@ def main():
         return bench_precision(args)
     if args.mode == "serving":
         return bench_serving_trace(args)
+    if args.mode == "prepare":
+        return bench_prepare(args)
     return bench_gpu(args)
 
 

@@ -68,10 +68,15 @@ enum { LBPM_DIST_F = 0, LBPM_DIST_A = 1, LBPM_DIST_B = 2 };
  * each fluid, nu = (tau - 1/2)/3 (the relaxation matrix "is determined based
  * on the kinematic viscosity"); alpha sets the interfacial tension
  * sigma_ab = 6 alpha; beta sets the interface thickness; force is the
- * constant body force F. Unsteady-flow reservoirs (Sec. 4.1): with
- * reservoir_z = 1 the four z-layers at z = 0 hold fluid A at density rho_in
- * and the four at z = nz - 1 hold fluid B at rho_out; the z axis must then be
- * non-periodic.
+ * constant body force F. Unsteady-flow boundaries (Sec. 4.1), z axis
+ * non-periodic: reservoir_z = 1, reservoir slabs - after each step the four
+ * z-layers at z = 0 are reset to fluid A at rest at density rho_in and the
+ * four at z = nz - 1 to fluid B at rho_out; reservoir_z = 2, constant
+ * pressure at the faces (Zou and He's scheme, cited in Sec. 4.1) - after each
+ * step the populations entering the face sites z = 0 and z = nz - 1 from
+ * outside are rebuilt so that those sites have density rho_in (rho_out) and no
+ * tangential velocity, and fluid A enters at the inlet, fluid B at the
+ * outlet.
  * Valid ranges: tau > 0.5; alpha >= 0; beta >= 0 (0 disables recoloring);
  * finite force; precision LBPM_FP32 or LBPM_FP16; periodic[i] in {0, 1};
  * rho_in, rho_out > 0. Otherwise LBPM_E_INVALID.
@@ -82,7 +87,7 @@ typedef struct {
     double force[3];
     int precision;
     int periodic[3];      /* 1 = periodic axis; a non-periodic face is a solid wall (phi_s = 0) */
-    int reservoir_z;
+    int reservoir_z;      /* 0 none, 1 reservoir slabs, 2 pressure faces */
     double rho_in, rho_out;
 } lbpm_params;
 

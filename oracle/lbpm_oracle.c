@@ -42,7 +42,21 @@
  *   - reservoir slabs (Sec. 4.1 names pressure reservoirs at inlet and
  *     outlet without giving a scheme): after streaming, the sites with
  *     z < 4 are reset to f = t_q rho_in, A = w_q, B = 0 and the sites with
- *     z >= nz - 4 to f = t_q rho_out, A = 0, B = w_q.
+ *     z >= nz - 4 to f = t_q rho_out, A = 0, B = w_q;
+ *   - pressure boundary (reservoir_z = 2; Sec. 4.1 cites Zou and He's
+ *     scheme for constant inlet / outlet pressure): after streaming (and on
+ *     the initial state), at every pore site of the face z = 0 (density
+ *     rho_in) or z = nz - 1 (rho_out), the populations entering from outside
+ *     are rebuilt so that the site has that density and no tangential
+ *     velocity, by bouncing back their non-equilibrium parts: with n the
+ *     inward normal, S0 the sum over c.n = 0 and S_out the sum over
+ *     c.n = -1, u_n = 1 - (S0 + 2 S_out) / rho and, for each entering q,
+ *     f_q = f_qbar + 2 t_q rho u_n (c_q.n) / c_s^2 - c_t N_t, which is
+ *     rho u_n / 3 for the normal and rho u_n / 6 for the four edges, with
+ *     N_t = (1/2) sum_{c.n = 0} c_t f for t = x, y. The
+ *     entering component population is the reservoir fluid's equilibrium at
+ *     the face velocity: A = w rho_in (1 + 4.5 u_z) and B = 0 at the inlet,
+ *     B = w rho_out (1 - 4.5 u_z) and A = 0 at the outlet.
  *
  * Parity status: every function here is pinned by the tests against closed
  * forms, physics or an independent dense implementation, except the
@@ -400,7 +414,7 @@ void orc_set_params(orc_t* o, double tau_a, double tau_b, double alpha, double b
 void orc_set_rate_mode(orc_t* o, int mode) { o->rate_mode = mode; }
 
 static void reset_reservoirs(orc_t* o, double* f, double* A, double* B) {
-    if (!o->reservoir_z) return;
+    if (o->reservoir_z != 1) return;
     for (long long n = 0; n < o->N; ++n) {
         const int z = o->sz[n];
         int side = 0;
@@ -416,6 +430,45 @@ static void reset_reservoirs(orc_t* o, double* f, double* A, double* B) {
     }
 }
 
+/* Pressure boundary at the z faces (reservoir_z == 2), on a state in
+ * canonical post-streaming form. */
+static void pressure_faces(orc_t* o, double* f, double* A, double* B) {
+    if (o->reservoir_z != 2) return;
+    for (long long n = 0; n < o->N; ++n) {
+        const int z = o->sz[n];
+        int nrm;                                   /* inward normal along z */
+        double rho;
+        if (z == 0) { nrm = 1; rho = o->rho_in; }
+        else if (z == o->nz - 1) { nrm = -1; rho = o->rho_out; }
+        else continue;
+        double* g = f + n * Q19;
+        double s0 = 0.0, sout = 0.0, Nt[2] = {0.0, 0.0};
+        for (int q = 0; q < Q19; ++q) {
+            const int cn = XI[q][2] * nrm;
+            if (cn == 0) {
+                s0 += g[q];
+                Nt[0] += XI[q][0] * g[q];
+                Nt[1] += XI[q][1] * g[q];
+            } else if (cn < 0) {
+                sout += g[q];
+            }
+        }
+        Nt[0] *= 0.5;
+        Nt[1] *= 0.5;
+        const double un = 1.0 - (s0 + 2.0 * sout) / rho;
+        for (int q = 1; q < Q19; ++q) {
+            if (XI[q][2] * nrm <= 0) continue;     /* only the entering directions */
+            const int tang = abs(XI[q][0]) + abs(XI[q][1]);
+            g[q] = g[opposite(q)] + rho * un * (tang ? 1.0 / 6.0 : 1.0 / 3.0) - XI[q][0] * Nt[0] - XI[q][1] * Nt[1];
+        }
+        const double uz = nrm * un;
+        const int qin = nrm > 0 ? 5 : 6;           /* D3Q7 direction entering the face */
+        const double eq = W7[qin] * rho * (1.0 + 4.5 * XI[qin][2] * uz);
+        A[n * Q7 + qin] = nrm > 0 ? eq : 0.0;
+        B[n * Q7 + qin] = nrm > 0 ? 0.0 : eq;
+    }
+}
+
 /* Initial state consistent with a phase field phi0 (per voxel; pores read). */
 void orc_init_fluids(orc_t* o, const float* phi0) {
     for (long long n = 0; n < o->N; ++n) {
@@ -428,6 +481,7 @@ void orc_init_fluids(orc_t* o, const float* phi0) {
         }
     }
     reset_reservoirs(o, o->f, o->A, o->B);
+    pressure_faces(o, o->f, o->A, o->B);
     o->step = 0;
 }
 
@@ -542,6 +596,7 @@ static void one_step(orc_t* o) {
         }
     }
     reset_reservoirs(o, o->fn, o->An, o->Bn);
+    pressure_faces(o, o->fn, o->An, o->Bn);
     double* t;
     t = o->f; o->f = o->fn; o->fn = t;
     t = o->A; o->A = o->An; o->An = t;

@@ -200,7 +200,10 @@ lbpm_status check_params(lbpm_ctx* c, const lbpm_params* p) {
     }
     if (p->precision != LBPM_FP32 && p->precision != LBPM_FP16)
         return fail(c, LBPM_E_INVALID, "precision must be LBPM_FP32 or LBPM_FP16");
-    if (p->reservoir_z != 0 && p->reservoir_z != 1) return fail(c, LBPM_E_INVALID, "reservoir_z must be 0 or 1");
+    if (p->reservoir_z < 0 || p->reservoir_z > 2) return fail(c, LBPM_E_INVALID, "reservoir_z must be 0, 1 or 2");
+    if (p->reservoir_z == 2 && !(p->rho_in > 0.0 && p->rho_out > 0.0 && std::isfinite(p->rho_in) &&
+                                 std::isfinite(p->rho_out)))
+        return fail(c, LBPM_E_INVALID, "the pressure boundary needs finite rho_in, rho_out > 0");
     if (p->reservoir_z && p->periodic[2]) return fail(c, LBPM_E_INVALID, "reservoirs need a non-periodic z axis");
     if (!(p->rho_in > 0.0) || !(p->rho_out > 0.0)) return fail(c, LBPM_E_INVALID, "rho_in and rho_out must be > 0");
     return LBPM_OK;

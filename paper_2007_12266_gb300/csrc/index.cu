@@ -194,27 +194,27 @@ __global__ void k_affinity_map(const uint16_t* labels, long long V, int nx, int 
     phi[padded_of(v, nx, ny, px, py)] = map[v];
 }
 
-__device__ __forceinline__ int slab_side(int pv, int px, int pxpy, int nz) {
+// 1: inlet (the first `depth` z layers), 2: outlet (the last ones), 0: neither
+__device__ __forceinline__ int slab_side(int pv, int pxpy, int nz, int depth) {
     const int z = pv / pxpy - 1;
-    (void)px;
-    if (z < 4) return 1;
-    if (z >= nz - 4) return 2;
+    if (z < depth) return 1;
+    if (z >= nz - depth) return 2;
     return 0;
 }
 
-__global__ void k_slab_flags(const int* site_vox, long long N, int px, int pxpy, int nz, int* flags) {
+__global__ void k_slab_flags(const int* site_vox, long long N, int pxpy, int nz, int depth, int* flags) {
     const long long n = static_cast<long long>(blockIdx.x) * kBlock + threadIdx.x;
     if (n >= N) return;
-    flags[n] = slab_side(site_vox[n], px, pxpy, nz) != 0 ? 1 : 0;
+    flags[n] = slab_side(site_vox[n], pxpy, nz, depth) != 0 ? 1 : 0;
 }
 
-__global__ void k_slab_scatter(const int* site_vox, long long N, int px, int pxpy, int nz,
+__global__ void k_slab_scatter(const int* site_vox, long long N, int pxpy, int nz, int depth,
                                const int* flags, const int* scan, int* sites, signed char* side) {
     const long long n = static_cast<long long>(blockIdx.x) * kBlock + threadIdx.x;
     if (n >= N || !flags[n]) return;
     const int e = scan[n];
     sites[e] = static_cast<int>(n);
-    side[e] = static_cast<signed char>(slab_side(site_vox[n], px, pxpy, nz));
+    side[e] = static_cast<signed char>(slab_side(site_vox[n], pxpy, nz, depth));
 }
 
 __global__ void k_export_index(const int* site_vox, const int* vsite, long long N, int nx, int ny,
@@ -299,14 +299,17 @@ cudaError_t launch_affinity_map(const lbpm_ctx* c, const float* map, cudaStream_
     return cudaGetLastError();
 }
 
+// reservoir slabs are four layers deep; the pressure boundary acts on the face layer
+int slab_depth(const lbpm_ctx* c) { return c->params.reservoir_z == 2 ? 1 : 4; }
+
 cudaError_t launch_slab_flags(const lbpm_ctx* c, int* flags, cudaStream_t s) {
-    k_slab_flags<<<blocks_for(c->N), kBlock, 0, s>>>(c->d_site_vox, c->N, c->px, c->px * c->py, c->nz,
+    k_slab_flags<<<blocks_for(c->N), kBlock, 0, s>>>(c->d_site_vox, c->N, c->px * c->py, c->nz, slab_depth(c),
                                                      flags);
     return cudaGetLastError();
 }
 
 cudaError_t launch_slab_scatter(const lbpm_ctx* c, const int* flags, const int* scan, cudaStream_t s) {
-    k_slab_scatter<<<blocks_for(c->N), kBlock, 0, s>>>(c->d_site_vox, c->N, c->px, c->px * c->py, c->nz,
+    k_slab_scatter<<<blocks_for(c->N), kBlock, 0, s>>>(c->d_site_vox, c->N, c->px * c->py, c->nz, slab_depth(c),
                                                        flags, scan, c->d_slab_site, c->d_slab_side);
     return cudaGetLastError();
 }

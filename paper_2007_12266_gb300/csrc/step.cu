@@ -42,6 +42,15 @@ __global__ void __launch_bounds__(kBlock, 4) k_collide(DomainView d) {
 }
 
 template <int PAR, class S>
+__global__ void __launch_bounds__(kBlock) k_pressure_faces(DomainView d, const int* sites,
+                                                           const signed char* side, int n_face,
+                                                           float rho_in, float rho_out, float drho_in,
+                                                           float drho_out) {
+    const int i = blockIdx.x * kBlock + threadIdx.x;
+    if (i < n_face) pressure_face_thread<PAR, S>(d, sites[i], side[i], rho_in, rho_out, drho_in, drho_out);
+}
+
+template <int PAR, class S>
 __global__ void __launch_bounds__(kBlock) k_reservoir(DomainView d, const int* sites,
                                                       const signed char* side, int n_slab,
                                                       float rho_in, float rho_out) {
@@ -177,7 +186,8 @@ cudaError_t launch_collide(const lbpm_ctx* c, int parity, cudaStream_t s) {
     return h ? launch_pdl(k_collide<1, StoreF16>, g, s, d) : launch_pdl(k_collide<1, StoreF32>, g, s, d);
 }
 
-// parity = parity of the step that will READ the reset values
+// parity = parity of the step that will READ the reset values; reservoir slabs
+// (reservoir_z = 1) or the pressure boundary at the z faces (reservoir_z = 2)
 cudaError_t launch_reservoir(const lbpm_ctx* c, int parity, cudaStream_t s) {
     if (c->n_slab == 0) return cudaSuccess;
     DomainView d = make_view(c);
@@ -185,6 +195,20 @@ cudaError_t launch_reservoir(const lbpm_ctx* c, int parity, cudaStream_t s) {
     const int ns = static_cast<int>(c->n_slab);
     const float ri = static_cast<float>(c->params.rho_in), ro = static_cast<float>(c->params.rho_out);
     const bool h = c->params.precision == LBPM_FP16;
+    if (c->params.reservoir_z == 2) {   // pressure boundary at the z faces
+        // rho - 1 formed in double, so the small difference keeps full fp32 precision
+        const float di = static_cast<float>(c->params.rho_in - 1.0), dout = static_cast<float>(c->params.rho_out - 1.0);
+        const int* st = c->d_slab_site;
+        const signed char* sd = c->d_slab_side;
+        if (parity == 0) {
+            if (h) k_pressure_faces<0, StoreF16><<<g, kBlock, 0, s>>>(d, st, sd, ns, ri, ro, di, dout);
+            else k_pressure_faces<0, StoreF32><<<g, kBlock, 0, s>>>(d, st, sd, ns, ri, ro, di, dout);
+        } else {
+            if (h) k_pressure_faces<1, StoreF16><<<g, kBlock, 0, s>>>(d, st, sd, ns, ri, ro, di, dout);
+            else k_pressure_faces<1, StoreF32><<<g, kBlock, 0, s>>>(d, st, sd, ns, ri, ro, di, dout);
+        }
+        return cudaGetLastError();
+    }
     if (parity == 0) {
         if (h) k_reservoir<0, StoreF16><<<g, kBlock, 0, s>>>(d, c->d_slab_site, c->d_slab_side, ns, ri, ro);
         else k_reservoir<0, StoreF32><<<g, kBlock, 0, s>>>(d, c->d_slab_site, c->d_slab_side, ns, ri, ro);

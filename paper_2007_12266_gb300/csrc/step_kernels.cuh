@@ -580,4 +580,89 @@ __device__ __forceinline__ void reservoir_thread(const DomainView& d, int n, int
     });
 }
 
+// ---------------------------------------------------------------------------
+// pressure boundary at the z faces (Sec. 4.1: constant inlet and outlet
+// pressures; Zou and He's non-equilibrium bounce-back): after streaming, the
+// five populations that enter a face site from outside the domain (c_z = +1
+// at the inlet z = 0, c_z = -1 at the outlet z = nz - 1) are set so that the
+// site's density is the face density and its tangential velocity is zero:
+//   u_z = +-(1 - (S_0 + 2 S_out) / rho)      S_0: c_z = 0, S_out: leaving
+//   f_in(normal) = f_out(normal) +- rho u_z / 3
+//   f_in(edge)   = f_out(opposite edge) +- rho u_z / 6 -+ N_t,
+//   N_t = (1/2) sum_{c_z = 0} c_t f   (t = x, y, the tangential momentum)
+// The one entering D3Q7 population of each component is the reservoir
+// fluid's equilibrium at the face velocity: inlet A = w rho_in (1 + 4.5 u_z),
+// B = 0; outlet B = w rho_out (1 - 4.5 u_z), A = 0. The values go into the
+// slots the NEXT step (parity PAR) reads.
+// ---------------------------------------------------------------------------
+template <int PAR, class S>
+__device__ __forceinline__ void pressure_face_thread(const DomainView& d, int n, int side, float rho_in,
+                                                     float rho_out, float drho_in, float drho_out) {
+    const int v = d.site_vox[n];
+    int nb[Q19];
+    if constexpr (PAR == 1 || S::kRef) {
+        static_for<1, Q19>([&](auto qc) {
+            constexpr int q = decltype(qc)::value;
+            nb[q] = __ldg(d.vsite + v + stencil_off(d, q));
+        });
+    }
+    // incoming populations of the next step as deviations d_q = f_q - t_q: the
+    // weights of the sums below add up to one, so u_n is formed from small
+    // numbers and rho - 1 (exact in fp32) instead of cancelling O(1) sums
+    float dv[Q19];
+    static_for<0, Q19>([&](auto qc) {
+        constexpr int q = decltype(qc)::value;
+        dv[q] = S::template ld_fdev<q>(d.f, read_slot<PAR, q>(d, n, nb));
+        if constexpr (S::kRef) dv[q] = fmaf(t19(q), d.drho[f_ref_read<PAR, q>(n, nb)], dv[q]);
+    });
+    const float sgn = side == 1 ? 1.0f : -1.0f;       // face normal into the domain
+    const float rho = side == 1 ? rho_in : rho_out;
+    const float drho = side == 1 ? drho_in : drho_out;
+    float D = 0.0f, nx = 0.0f, ny = 0.0f;
+    static_for<0, Q19>([&](auto qc) {
+        constexpr int q = decltype(qc)::value;
+        if constexpr (cz(q) == 0) {
+            D += dv[q];
+            if constexpr (cx(q) != 0) nx += cx(q) * dv[q];
+            if constexpr (cy(q) != 0) ny += cy(q) * dv[q];
+        } else {
+            if (cz(q) * sgn < 0.0f) D += 2.0f * dv[q];   // leaving the domain through this face
+        }
+    });
+    nx *= 0.5f;
+    ny *= 0.5f;
+    const float un = (drho - D) / rho;                // velocity along the inward normal
+    const float j3 = rho * un * (1.0f / 3.0f), j6 = rho * un * (1.0f / 6.0f);
+    static_for<1, Q19>([&](auto qc) {
+        constexpr int q = decltype(qc)::value;
+        if constexpr (cz(q) != 0) {
+            if (cz(q) * sgn > 0.0f) {
+                float dev = dv[opp(q)] + (cx(q) == 0 && cy(q) == 0 ? j3 : j6);
+                if constexpr (cx(q) != 0) dev -= cx(q) * nx;
+                if constexpr (cy(q) != 0) dev -= cy(q) * ny;
+                const size_t i = read_slot<PAR, q>(d, n, nb);
+                if constexpr (S::kRef) dev = fmaf(-t19(q), d.drho[f_ref_read<PAR, q>(n, nb)], dev);
+                S::template st_fdev<q>(d.f, i, dev);
+            }
+        }
+    });
+    // the entering component population
+    const float uz = sgn * un;
+    static_for<5, 7>([&](auto qc) {
+        constexpr int q = decltype(qc)::value;   // 5: +z, 6: -z
+        if (cz(q) * sgn > 0.0f) {
+            const float eq = w7(q) * rho * (1.0f + 4.5f * cz(q) * uz);
+            float av = side == 1 ? eq : 0.0f, bv = side == 1 ? 0.0f : eq;
+            if constexpr (S::kRef) {
+                const float2 r = nab_prev<PAR>(d)[writer_of<q>(n, nb)];
+                av -= w7(q) * r.x;
+                bv -= w7(q) * r.y;
+            }
+            const size_t i = read_slot<PAR, q>(d, n, nb);
+            S::template st_c<q>(d.a, i, av);
+            S::template st_c<q>(d.b, i, bv);
+        }
+    });
+}
+
 }  // namespace lbm
