@@ -405,6 +405,30 @@ lbpm_status lbpm_server_stats(const lbpm_server* server, long long* site_updates
 lbpm_status lbpm_force_rescale(const double force[3], double ca, double ca_target, double max_factor,
                                double out[3], double* factor);
 
+/* Shell aggregation, one morphological step (Sec. 3.3): moves the interface
+ * of fluid A (phi > 0) by the signed distance delta in voxels (dilation > 0,
+ * erosion < 0) through its distance map Phi_A (< 0 inside A): Eq. lb-dist
+ * solved for the distance where |phi| < tanh(3 beta), and beyond that the
+ * nearest such band voxel within 4 voxels plus its own distance; sites with
+ * no band voxel within 4 voxels keep their phase. The new phase is
+ * phi' = -tanh(beta (Phi - delta)) (Eq. lb-dist-to-phase); with apply != 0
+ * the component populations of the changed sites become w_q Na', w_q Nb' at
+ * rest with Na' + Nb' equal to the site's current Na + Nb (the momentum
+ * populations are left alone). *before / *after (may be NULL) receive the
+ * number of sites with phi > 0 before and after. |delta| <= 3.
+ * Errors: LBPM_E_INVALID, LBPM_E_STATE (no fluids), LBPM_E_OOM, LBPM_E_CUDA. */
+lbpm_status lbpm_morph(lbpm_ctx* ctx, double delta, int apply, long long* before, long long* after);
+
+/* Shell aggregation protocol (Sec. 3.3): change the volume of fluid A by the
+ * factor target_ratio (> 1 grows it). Each round applies a dummy growth of
+ * one voxel (not kept) to measure the volume response, rescales delta
+ * linearly to the volume still missing, applies it, and relaxes the state by
+ * relax_steps (even) LB steps; rounds stop once the measured volume ratio
+ * reaches the target, or after max_rounds. *achieved (may be NULL) receives
+ * the final ratio of A sites to those at the start, *rounds the rounds run. */
+lbpm_status lbpm_shell_aggregation(lbpm_ctx* ctx, double target_ratio, long long relax_steps, int max_rounds,
+                                   double* achieved, int* rounds);
+
 /* ------------------------------------------------------------------------
  * Image preparation (Sec. 4.2 mixing region; Sec. 3.3 mixed-wet relabel).
  * Both run CUDA kernels on `device` on a copy of the caller's host image,

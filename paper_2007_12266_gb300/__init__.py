@@ -244,6 +244,22 @@ class Domain:
     def sync(self):
         self._check(self._L.lbpm_sync(self._h))
 
+    # -- shell aggregation (morphological steps on fluid A) ----------------
+    def morph(self, delta: float, apply: bool = True):
+        """Move the interface of fluid A by delta voxels (library call
+        lbpm_morph); returns (A sites before, A sites after)."""
+        b, a = ct.c_longlong(), ct.c_longlong()
+        self._check(self._L.lbpm_morph(self._h, float(delta), int(bool(apply)), ct.byref(b), ct.byref(a)))
+        return b.value, a.value
+
+    def shell_aggregation(self, target_ratio: float, relax_steps: int = 1000, max_rounds: int = 8):
+        """Change the volume of fluid A by target_ratio (lbpm_shell_aggregation);
+        returns (achieved ratio, rounds)."""
+        r, n = ct.c_double(), ct.c_int()
+        self._check(self._L.lbpm_shell_aggregation(self._h, float(target_ratio), int(relax_steps), int(max_rounds),
+                                                    ct.byref(r), ct.byref(n)))
+        return r.value, n.value
+
     def measure(self, raise_unstable: bool = False) -> dict:
         m = Measures()
         st = self._L.lbpm_measure(self._h, ct.byref(m))

@@ -1,8 +1,10 @@
 // C ABI of the library (declared in include/lbpm.h): context, memory, image
 // loading and indexing, parameters, time stepping, measures and exchange.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <vector>
 #include <new>
 
 #include "internal.h"
@@ -746,6 +748,89 @@ lbpm_status lbpm_restore(lbpm_ctx* c, const void* host_buf, size_t bytes) {
     if ((s = lbpm_write_distributions(c, LBPM_DIST_B, p + 26 * c->N))) return s;
     c->have_fluids = true;
     c->unstable = false;
+    return LBPM_OK;
+}
+
+namespace {
+constexpr int kMorphRadius = 4;   // far-field search radius of the distance map (voxels)
+}
+
+lbpm_status lbpm_morph(lbpm_ctx* c, double delta, int apply, long long* before, long long* after) {
+    lbpm_status s = enter(c);
+    if (s) return s;
+    if (!(std::fabs(delta) <= 3.0)) return fail(c, LBPM_E_INVALID, "|delta| must be <= 3 voxels");
+    if (!c->have_fluids) return fail(c, LBPM_E_STATE, "initialise the fluids first");
+    if (!(c->params.beta > 0.0)) return fail(c, LBPM_E_INVALID, "the distance map needs beta > 0");
+    // ball offsets of the far-field search and their lengths
+    std::vector<int3> off;
+    std::vector<float> len;
+    for (int z = -kMorphRadius; z <= kMorphRadius; ++z)
+        for (int y = -kMorphRadius; y <= kMorphRadius; ++y)
+            for (int x = -kMorphRadius; x <= kMorphRadius; ++x) {
+                const int r2 = x * x + y * y + z * z;
+                if (r2 == 0 || r2 > kMorphRadius * kMorphRadius) continue;
+                off.push_back(make_int3(x, y, z));
+                len.push_back(static_cast<float>(std::sqrt(static_cast<double>(r2))));
+            }
+    float *d_phi, *d_dist, *d_ntot, *d_len;
+    int3* d_off;
+    unsigned long long* d_cnt;
+    LBPM_ALLOC(c, d_phi, float, c->V);
+    d_dist = static_cast<float*>(dalloc(c, sizeof(float) * c->V));
+    d_ntot = static_cast<float*>(dalloc(c, sizeof(float) * std::max<long long>(c->N, 1)));
+    d_len = static_cast<float*>(dalloc(c, sizeof(float) * len.size()));
+    d_off = static_cast<int3*>(dalloc(c, sizeof(int3) * off.size()));
+    d_cnt = static_cast<unsigned long long*>(dalloc(c, 2 * sizeof(unsigned long long)));
+    unsigned long long cnt[2] = {0, 0};
+    cudaError_t e = (d_dist && d_ntot && d_len && d_off && d_cnt) ? cudaSuccess : cudaErrorMemoryAllocation;
+    // voxels without a site: NaN distance (fminf ignores it)
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_dist, 0xff, sizeof(float) * c->V, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_cnt, 0, 2 * sizeof(unsigned long long), c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d_off, off.data(), sizeof(int3) * off.size(), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d_len, len.data(), sizeof(float) * len.size(), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess)
+        e = launch_morph(c, static_cast<int>(c->step & 1), static_cast<float>(delta), kMorphRadius, apply != 0,
+                         d_phi, d_dist, d_ntot, d_off, d_len, static_cast<int>(off.size()), d_cnt, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(cnt, d_cnt, sizeof cnt, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    for (void* p : {static_cast<void*>(d_phi), static_cast<void*>(d_dist), static_cast<void*>(d_ntot),
+                    static_cast<void*>(d_len), static_cast<void*>(d_off), static_cast<void*>(d_cnt)})
+        dfree(c, p);
+    if (e != cudaSuccess) return fail_cuda(c, "morph", e);
+    c->launches += 2;
+    if (before) *before = static_cast<long long>(cnt[0]);
+    if (after) *after = static_cast<long long>(cnt[1]);
+    return LBPM_OK;
+}
+
+lbpm_status lbpm_shell_aggregation(lbpm_ctx* c, double target_ratio, long long relax_steps, int max_rounds,
+                                   double* achieved, int* rounds) {
+    lbpm_status s = enter(c);
+    if (s) return s;
+    if (!(target_ratio > 0.0) || !std::isfinite(target_ratio) || relax_steps < 0 || max_rounds < 1)
+        return fail(c, LBPM_E_INVALID, "bad shell aggregation settings");
+    long long v0 = 0, cur = 0, v1 = 0;
+    if ((s = lbpm_morph(c, 0.0, 0, &v0, nullptr))) return s;
+    if (v0 == 0) return fail(c, LBPM_E_STATE, "fluid A occupies no site");
+    const double goal = target_ratio * static_cast<double>(v0);
+    const double sgn = target_ratio >= 1.0 ? 1.0 : -1.0;
+    cur = v0;
+    int r = 0;
+    while (r < max_rounds && (sgn > 0 ? cur < goal : cur > goal)) {
+        ++r;
+        // dummy growth of one voxel, not kept: the volume response
+        if ((s = lbpm_morph(c, sgn, 0, &cur, &v1))) return s;
+        if (v1 == cur) break;   // no interface left to move
+        double delta = sgn * std::fabs(goal - static_cast<double>(cur)) / std::fabs(static_cast<double>(v1 - cur));
+        delta = std::max(-3.0, std::min(3.0, delta));
+        if ((s = lbpm_morph(c, delta, 1, nullptr, nullptr))) return s;
+        if (relax_steps > 0 && (s = lbpm_advance(c, relax_steps))) return s;
+        if ((s = lbpm_morph(c, 0.0, 0, &cur, nullptr))) return s;
+    }
+    if (achieved) *achieved = static_cast<double>(cur) / static_cast<double>(v0);
+    if (rounds) *rounds = r;
     return LBPM_OK;
 }
 
