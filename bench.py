@@ -429,6 +429,23 @@ def bench_prepare(args):
             ts.append(time.perf_counter() - t1)
         med = statistics.median(ts)
         out[name] = {"seconds_per_call": med, "value": V / med / 1e9, "changed_voxels": int(np.count_nonzero(r != lab))}
+    # shell aggregation step on the 256^3 steady-state workload after 100 steps
+    from synthetic import workload_steady256
+    w = workload_steady256(256)
+    dom = lbm.Domain(w.labels, w.affinity, periodic=w.periodic, tau_a=w.tau_a, tau_b=w.tau_b, alpha=w.alpha,
+                     beta=w.beta, force=w.force)
+    dom.init_fluids(w.phi0)
+    dom.advance(100)
+    dom.morph(1.0, apply=False)
+    ts = []
+    for _ in range(5):
+        t1 = time.perf_counter()
+        b, a = dom.morph(1.0, apply=False)
+        ts.append(time.perf_counter() - t1)
+    med = statistics.median(ts)
+    out["morph_256"] = {"seconds_per_call": med, "sites": dom.n_sites, "value": dom.n_sites / med / 1e9,
+                        "unit": "Gsite/s", "a_sites_before": b, "a_sites_after_delta_1": a}
+    dom.close()
     print(json.dumps(out))
     return 0
 

@@ -764,6 +764,7 @@ lbpm_status lbpm_morph(lbpm_ctx* c, double delta, int apply, long long* before, 
     // ball offsets of the far-field search and their lengths
     std::vector<int3> off;
     std::vector<float> len;
+    std::vector<long long> lin;
     for (int z = -kMorphRadius; z <= kMorphRadius; ++z)
         for (int y = -kMorphRadius; y <= kMorphRadius; ++y)
             for (int x = -kMorphRadius; x <= kMorphRadius; ++x) {
@@ -771,18 +772,21 @@ lbpm_status lbpm_morph(lbpm_ctx* c, double delta, int apply, long long* before, 
                 if (r2 == 0 || r2 > kMorphRadius * kMorphRadius) continue;
                 off.push_back(make_int3(x, y, z));
                 len.push_back(static_cast<float>(std::sqrt(static_cast<double>(r2))));
+                lin.push_back(x + static_cast<long long>(c->nx) * (y + static_cast<long long>(c->ny) * z));
             }
     float *d_phi, *d_dist, *d_ntot, *d_len;
     int3* d_off;
+    long long* d_lin;
     unsigned long long* d_cnt;
     LBPM_ALLOC(c, d_phi, float, c->V);
     d_dist = static_cast<float*>(dalloc(c, sizeof(float) * c->V));
     d_ntot = static_cast<float*>(dalloc(c, sizeof(float) * std::max<long long>(c->N, 1)));
     d_len = static_cast<float*>(dalloc(c, sizeof(float) * len.size()));
     d_off = static_cast<int3*>(dalloc(c, sizeof(int3) * off.size()));
+    d_lin = static_cast<long long*>(dalloc(c, sizeof(long long) * lin.size()));
     d_cnt = static_cast<unsigned long long*>(dalloc(c, 2 * sizeof(unsigned long long)));
     unsigned long long cnt[2] = {0, 0};
-    cudaError_t e = (d_dist && d_ntot && d_len && d_off && d_cnt) ? cudaSuccess : cudaErrorMemoryAllocation;
+    cudaError_t e = (d_dist && d_ntot && d_len && d_off && d_lin && d_cnt) ? cudaSuccess : cudaErrorMemoryAllocation;
     // voxels without a site: NaN distance (fminf ignores it)
     if (e == cudaSuccess) e = cudaMemsetAsync(d_dist, 0xff, sizeof(float) * c->V, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(d_cnt, 0, 2 * sizeof(unsigned long long), c->stream);
@@ -791,12 +795,15 @@ lbpm_status lbpm_morph(lbpm_ctx* c, double delta, int apply, long long* before, 
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(d_len, len.data(), sizeof(float) * len.size(), cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d_lin, lin.data(), sizeof(long long) * lin.size(), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess)
         e = launch_morph(c, static_cast<int>(c->step & 1), static_cast<float>(delta), kMorphRadius, apply != 0,
-                         d_phi, d_dist, d_ntot, d_off, d_len, static_cast<int>(off.size()), d_cnt, c->stream);
+                         d_phi, d_dist, d_ntot, d_off, d_lin, d_len, static_cast<int>(off.size()), d_cnt, c->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(cnt, d_cnt, sizeof cnt, cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     for (void* p : {static_cast<void*>(d_phi), static_cast<void*>(d_dist), static_cast<void*>(d_ntot),
-                    static_cast<void*>(d_len), static_cast<void*>(d_off), static_cast<void*>(d_cnt)})
+                    static_cast<void*>(d_len), static_cast<void*>(d_off), static_cast<void*>(d_lin),
+                    static_cast<void*>(d_cnt)})
         dfree(c, p);
     if (e != cudaSuccess) return fail_cuda(c, "morph", e);
     c->launches += 2;

@@ -127,7 +127,7 @@ cudaError_t launch_phase(const lbpm_ctx* c, int parity, cudaStream_t s);
 cudaError_t launch_collide(const lbpm_ctx* c, int parity, cudaStream_t s);
 cudaError_t launch_reservoir(const lbpm_ctx* c, int parity, cudaStream_t s);
 cudaError_t launch_morph(const lbpm_ctx* c, int parity, float delta, int R, int apply, float* phi_grid,
-                         float* dist_grid, float* ntot, int3* off, float* off_len, int n_off,
+                         float* dist_grid, float* ntot, int3* off, long long* off_lin, float* off_len, int n_off,
                          unsigned long long* counts, cudaStream_t s);
 
 constexpr int NSUM = 27;  // per-site sums reduced by the measure kernel

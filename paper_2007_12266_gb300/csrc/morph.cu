@@ -69,8 +69,9 @@ __global__ void __launch_bounds__(kMorphBlock) k_morph_phase(DomainView d, Morph
 
 template <int PAR, class S>
 __global__ void __launch_bounds__(kMorphBlock) k_morph_apply(DomainView d, MorphGrid g, const int3* off,
-                                                             const float* off_len, int n_off, int R, float beta,
-                                                             float delta, int apply, unsigned long long* counts) {
+                                                             const long long* off_lin, const float* off_len,
+                                                             int n_off, int R, float beta, float delta, int apply,
+                                                             unsigned long long* counts) {
     const int n = blockIdx.x * kMorphBlock + threadIdx.x;
     int before = 0, after = 0;
     if (n < d.n_sites) {
@@ -84,10 +85,16 @@ __global__ void __launch_bounds__(kMorphBlock) k_morph_apply(DomainView d, Morph
         if (own < INFINITY) {
             Phi = phi > 0.0f ? -own : own;     // band: Eq. lb-dist
         } else {
-            // far field: nearest band voxel within R, through its own distance
+            // far field: nearest band voxel within R, through its own distance;
+            // voxels at least R from every face use linear offsets
             const int dims[3] = {g.nx, g.ny, g.nz};
             float best = INFINITY;
-            for (int i = 0; i < n_off; ++i) {
+            const bool interior = c[0] >= R && c[0] < g.nx - R && c[1] >= R && c[1] < g.ny - R && c[2] >= R &&
+                                  c[2] < g.nz - R;
+            if (interior) {
+                for (int i = 0; i < n_off; ++i) best = fminf(best, off_len[i] + g.dist[u + off_lin[i]]);
+            }
+            for (int i = 0; i < (interior ? 0 : n_off); ++i) {
                 long long w = 0;
                 bool inside = true;
                 const int o[3] = {off[i].x, off[i].y, off[i].z};
@@ -154,7 +161,7 @@ unsigned blocks_of(long long n) { return static_cast<unsigned>((n + kMorphBlock 
 }  // namespace
 
 cudaError_t launch_morph(const lbpm_ctx* c, int parity, float delta, int R, int apply, float* phi_grid,
-                         float* dist_grid, float* ntot, int3* off, float* off_len, int n_off,
+                         float* dist_grid, float* ntot, int3* off, long long* off_lin, float* off_len, int n_off,
                          unsigned long long* counts, cudaStream_t s) {
     DomainView d = make_view(c);
     MorphGrid g{c->nx, c->ny, c->nz, {c->params.periodic[0], c->params.periodic[1], c->params.periodic[2]},
@@ -174,11 +181,11 @@ cudaError_t launch_morph(const lbpm_ctx* c, int parity, float delta, int R, int 
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (parity == 0) {
-        if (h) k_morph_apply<0, StoreF16><<<gN, kMorphBlock, 0, s>>>(d, g, off, off_len, n_off, R, beta, delta, apply, counts);
-        else k_morph_apply<0, StoreF32><<<gN, kMorphBlock, 0, s>>>(d, g, off, off_len, n_off, R, beta, delta, apply, counts);
+        if (h) k_morph_apply<0, StoreF16><<<gN, kMorphBlock, 0, s>>>(d, g, off, off_lin, off_len, n_off, R, beta, delta, apply, counts);
+        else k_morph_apply<0, StoreF32><<<gN, kMorphBlock, 0, s>>>(d, g, off, off_lin, off_len, n_off, R, beta, delta, apply, counts);
     } else {
-        if (h) k_morph_apply<1, StoreF16><<<gN, kMorphBlock, 0, s>>>(d, g, off, off_len, n_off, R, beta, delta, apply, counts);
-        else k_morph_apply<1, StoreF32><<<gN, kMorphBlock, 0, s>>>(d, g, off, off_len, n_off, R, beta, delta, apply, counts);
+        if (h) k_morph_apply<1, StoreF16><<<gN, kMorphBlock, 0, s>>>(d, g, off, off_lin, off_len, n_off, R, beta, delta, apply, counts);
+        else k_morph_apply<1, StoreF32><<<gN, kMorphBlock, 0, s>>>(d, g, off, off_lin, off_len, n_off, R, beta, delta, apply, counts);
     }
     return cudaGetLastError();
 }
