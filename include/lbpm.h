@@ -76,7 +76,12 @@ enum { LBPM_DIST_F = 0, LBPM_DIST_A = 1, LBPM_DIST_B = 2 };
  * step the populations entering the face sites z = 0 and z = nz - 1 from
  * outside are rebuilt so that those sites have density rho_in (rho_out) and no
  * tangential velocity, and fluid A enters at the inlet, fluid B at the
- * outlet.
+ * outlet; reservoir_z = 3, constant flux at the inlet (the flux condition of
+ * Sec. 4.1: a total volumetric flow rate, not a velocity at each point) and
+ * constant pressure rho_out at the outlet - the inlet face is a pressure face
+ * whose uniform density is chosen at every step so that the face velocities
+ * sum to flux_in (lattice units: sum over the inlet sites of u_z), letting
+ * the local inlet velocities follow the interior flow.
  * Valid ranges: tau > 0.5; alpha >= 0; beta >= 0 (0 disables recoloring);
  * finite force; precision LBPM_FP32 or LBPM_FP16; periodic[i] in {0, 1};
  * rho_in, rho_out > 0. Otherwise LBPM_E_INVALID.
@@ -87,8 +92,9 @@ typedef struct {
     double force[3];
     int precision;
     int periodic[3];      /* 1 = periodic axis; a non-periodic face is a solid wall (phi_s = 0) */
-    int reservoir_z;      /* 0 none, 1 reservoir slabs, 2 pressure faces */
+    int reservoir_z;      /* 0 none, 1 reservoir slabs, 2 pressure faces, 3 flux inlet + pressure outlet */
     double rho_in, rho_out;
+    double flux_in;       /* reservoir_z = 3: total inlet flux, 0 <= flux_in < number of inlet sites */
 } lbpm_params;
 
 /*

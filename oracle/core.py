@@ -49,7 +49,7 @@ def load_library():
     lib.orc_step_count.argtypes = [ct.c_void_p]
     lib.orc_get_index.argtypes = [ct.c_void_p, _i64p, _i32p]
     lib.orc_set_params.argtypes = [ct.c_void_p, ct.c_double, ct.c_double, ct.c_double,
-                                   ct.c_double, _dp, ct.c_int, ct.c_double, ct.c_double]
+                                   ct.c_double, _dp, ct.c_int, ct.c_double, ct.c_double, ct.c_double]
     lib.orc_set_rate_mode.argtypes = [ct.c_void_p, ct.c_int]
     lib.orc_init_fluids.argtypes = [ct.c_void_p, _fp]
     lib.orc_set_state.argtypes = [ct.c_void_p, _dp, _dp, _dp, ct.c_longlong]
@@ -116,7 +116,7 @@ class Oracle:
 
     def __init__(self, labels: np.ndarray, affinity: Optional[np.ndarray], periodic,
                  tau_a=0.7, tau_b=0.7, alpha=0.005, beta=0.95, force=(0.0, 0.0, 0.0),
-                 reservoir_z=0, rho_in=1.0, rho_out=1.0):
+                 reservoir_z=0, rho_in=1.0, rho_out=1.0, flux_in=0.0):
         self._lib = load_library()
         labels = np.ascontiguousarray(labels, dtype=np.uint16)
         nz, ny, nx = labels.shape
@@ -130,7 +130,7 @@ class Oracle:
         per = np.ascontiguousarray(periodic, dtype=np.int32)
         self._h = self._lib.orc_create(nx, ny, nz, labels, aff_ptr, per)
         self.N = int(self._lib.orc_num_sites(self._h))
-        self.set_params(tau_a, tau_b, alpha, beta, force, reservoir_z, rho_in, rho_out)
+        self.set_params(tau_a, tau_b, alpha, beta, force, reservoir_z, rho_in, rho_out, flux_in)
 
     def close(self):
         if getattr(self, "_h", None):
@@ -144,13 +144,13 @@ class Oracle:
             pass
 
     def set_params(self, tau_a, tau_b, alpha, beta, force, reservoir_z=0, rho_in=1.0,
-                   rho_out=1.0):
+                   rho_out=1.0, flux_in=0.0):
         self.params = dict(tau_a=tau_a, tau_b=tau_b, alpha=alpha, beta=beta,
                            force=tuple(force), reservoir_z=reservoir_z,
-                           rho_in=rho_in, rho_out=rho_out)
+                           rho_in=rho_in, rho_out=rho_out, flux_in=flux_in)
         self._lib.orc_set_params(self._h, float(tau_a), float(tau_b), float(alpha),
                                  float(beta), np.ascontiguousarray(force, np.float64),
-                                 int(reservoir_z), float(rho_in), float(rho_out))
+                                 int(reservoir_z), float(rho_in), float(rho_out), float(flux_in))
 
     def set_rate_mode(self, mode: int):
         self._lib.orc_set_rate_mode(self._h, int(mode))

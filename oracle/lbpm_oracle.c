@@ -56,7 +56,13 @@
  *     N_t = (1/2) sum_{c.n = 0} c_t f for t = x, y. The
  *     entering component population is the reservoir fluid's equilibrium at
  *     the face velocity: A = w rho_in (1 + 4.5 u_z) and B = 0 at the inlet,
- *     B = w rho_out (1 - 4.5 u_z) and A = 0 at the outlet.
+ *     B = w rho_out (1 - 4.5 u_z) and A = 0 at the outlet;
+ *   - flux inlet (reservoir_z = 3; Sec. 4.1's flux condition sets a total
+ *     volumetric flow rate across the inlet): the inlet is a pressure face
+ *     whose uniform density is chosen at every step so that the face
+ *     velocities u_n = 1 - K_s / rho of its sites (K_s = S0 + 2 S_out) sum to
+ *     the prescribed flux Q: rho = sum_s K_s / (n_in - Q); the outlet keeps
+ *     the pressure rho_out.
  *
  * Parity status: every function here is pinned by the tests against closed
  * forms, physics or an independent dense implementation, except the
@@ -293,6 +299,7 @@ typedef struct orc {
     double tau_a, tau_b, alpha, beta, F[3];
     int reservoir_z;
     double rho_in, rho_out;
+    double flux_in;
     int rate_mode;
     double *f, *fn;     /* [N][19] */
     double *A, *An;     /* [N][7] */
@@ -400,7 +407,7 @@ void orc_get_index(const orc_t* o, int64_t* site_vox, int32_t* nbr) {
 }
 
 void orc_set_params(orc_t* o, double tau_a, double tau_b, double alpha, double beta,
-                    const double* F, int reservoir_z, double rho_in, double rho_out) {
+                    const double* F, int reservoir_z, double rho_in, double rho_out, double flux_in) {
     o->tau_a = tau_a;
     o->tau_b = tau_b;
     o->alpha = alpha;
@@ -409,6 +416,7 @@ void orc_set_params(orc_t* o, double tau_a, double tau_b, double alpha, double b
     o->reservoir_z = reservoir_z;
     o->rho_in = rho_in;
     o->rho_out = rho_out;
+    o->flux_in = flux_in;
 }
 
 void orc_set_rate_mode(orc_t* o, int mode) { o->rate_mode = mode; }
@@ -433,12 +441,29 @@ static void reset_reservoirs(orc_t* o, double* f, double* A, double* B) {
 /* Pressure boundary at the z faces (reservoir_z == 2), on a state in
  * canonical post-streaming form. */
 static void pressure_faces(orc_t* o, double* f, double* A, double* B) {
-    if (o->reservoir_z != 2) return;
+    if (o->reservoir_z != 2 && o->reservoir_z != 3) return;
+    double rho_in = o->rho_in;
+    if (o->reservoir_z == 3) {
+        /* flux inlet: the uniform inlet density whose Zou-He face velocities
+         * u_n = 1 - K_s / rho sum to the flux, K_s = S0 + 2 S_out of site s */
+        double K = 0.0;
+        long long n_in = 0;
+        for (long long n = 0; n < o->N; ++n) {
+            if (o->sz[n] != 0) continue;
+            const double* g = f + n * Q19;
+            for (int q = 0; q < Q19; ++q) {
+                if (XI[q][2] == 0) K += g[q];
+                else if (XI[q][2] < 0) K += 2.0 * g[q];
+            }
+            ++n_in;
+        }
+        if (n_in > 0) rho_in = K / ((double)n_in - o->flux_in);
+    }
     for (long long n = 0; n < o->N; ++n) {
         const int z = o->sz[n];
         int nrm;                                   /* inward normal along z */
         double rho;
-        if (z == 0) { nrm = 1; rho = o->rho_in; }
+        if (z == 0) { nrm = 1; rho = rho_in; }
         else if (z == o->nz - 1) { nrm = -1; rho = o->rho_out; }
         else continue;
         double* g = f + n * Q19;

@@ -66,7 +66,8 @@ def _close_all():
             pass
 
 
-def _params(tau_a, tau_b, alpha, beta, force, precision, periodic, reservoir_z, rho_in, rho_out) -> Params:
+def _params(tau_a, tau_b, alpha, beta, force, precision, periodic, reservoir_z, rho_in, rho_out,
+            flux_in=0.0) -> Params:
     p = Params()
     p.tau_a, p.tau_b, p.alpha, p.beta = float(tau_a), float(tau_b), float(alpha), float(beta)
     for a in range(3):
@@ -75,6 +76,7 @@ def _params(tau_a, tau_b, alpha, beta, force, precision, periodic, reservoir_z, 
     p.precision = PRECISION[precision] if isinstance(precision, str) else int(precision)
     p.reservoir_z = int(reservoir_z)
     p.rho_in, p.rho_out = float(rho_in), float(rho_out)
+    p.flux_in = float(flux_in)
     return p
 
 
@@ -152,7 +154,7 @@ class Domain:
     def __init__(self, labels: np.ndarray, affinity: Optional[np.ndarray] = None, *,
                  periodic=(1, 1, 1), tau_a=0.7, tau_b=0.7, alpha=0.005, beta=0.95,
                  force=(0.0, 0.0, 0.0), precision="fp32", reservoir_z=0, rho_in=1.0,
-                 rho_out=1.0, device: int = 0, stream=None, use_torch_allocator: bool = True):
+                 rho_out=1.0, flux_in=0.0, device: int = 0, stream=None, use_torch_allocator: bool = True):
         torch = _torch()
         self._L = _lib.load()
         self.device = int(device)
@@ -170,7 +172,7 @@ class Domain:
             self._check(self._L.lbpm_set_allocator(self._h, self._callbacks[0], self._callbacks[1], None))
         self.set_params(tau_a=tau_a, tau_b=tau_b, alpha=alpha, beta=beta, force=force,
                         precision=precision, periodic=periodic, reservoir_z=reservoir_z,
-                        rho_in=rho_in, rho_out=rho_out)
+                        rho_in=rho_in, rho_out=rho_out, flux_in=flux_in)
         self.load_image(labels)
         if affinity is not None:
             self.set_affinity_map(affinity)
@@ -209,12 +211,12 @@ class Domain:
         self.shape = labels.shape
 
     def set_params(self, *, tau_a, tau_b, alpha, beta, force, precision="fp32",
-                   periodic=(1, 1, 1), reservoir_z=0, rho_in=1.0, rho_out=1.0):
-        p = _params(tau_a, tau_b, alpha, beta, force, precision, periodic, reservoir_z, rho_in, rho_out)
+                   periodic=(1, 1, 1), reservoir_z=0, rho_in=1.0, rho_out=1.0, flux_in=0.0):
+        p = _params(tau_a, tau_b, alpha, beta, force, precision, periodic, reservoir_z, rho_in, rho_out, flux_in)
         self._check(self._L.lbpm_set_params(self._h, ct.byref(p)))
         self.params = dict(tau_a=tau_a, tau_b=tau_b, alpha=alpha, beta=beta, force=tuple(force),
                            precision=precision, periodic=tuple(periodic), reservoir_z=reservoir_z,
-                           rho_in=rho_in, rho_out=rho_out)
+                           rho_in=rho_in, rho_out=rho_out, flux_in=flux_in)
 
     def update_params(self, **kw):
         p = dict(self.params)
@@ -487,7 +489,7 @@ class Server:
     def submit(self, labels, phi0, affinity=None, *, kind="steady", max_steps=10000, flux_tol=1e-4,
                sw_tol=1e-4, force_factor=2.0, force_cap=1.6e-4, tau_a=0.7, tau_b=0.7, alpha=0.005,
                beta=0.95, force=(0.0, 0.0, 0.0), precision="fp32", periodic=(1, 1, 1), reservoir_z=0,
-               rho_in=1.0, rho_out=1.0, ca_target=0.0, relax_steps=0, ca_tol=0.05) -> int:
+               rho_in=1.0, rho_out=1.0, flux_in=0.0, ca_target=0.0, relax_steps=0, ca_tol=0.05) -> int:
         lab = np.ascontiguousarray(labels, dtype=np.uint16)
         ph = np.ascontiguousarray(phi0, dtype=np.float32)
         aff = None if affinity is None else np.ascontiguousarray(affinity, dtype=np.float32)
@@ -496,7 +498,8 @@ class Server:
         sp.labels, sp.nx, sp.ny, sp.nz = lab.ctypes.data, nx, ny, nz
         sp.affinity = aff.ctypes.data if aff is not None else None
         sp.phi0 = ph.ctypes.data
-        sp.params = _params(tau_a, tau_b, alpha, beta, force, precision, periodic, reservoir_z, rho_in, rho_out)
+        sp.params = _params(tau_a, tau_b, alpha, beta, force, precision, periodic, reservoir_z, rho_in, rho_out,
+                            flux_in)
         sp.kind = JOB_KINDS[kind] if isinstance(kind, str) else int(kind)
         sp.max_steps = int(max_steps)
         sp.flux_tol, sp.sw_tol = float(flux_tol), float(sw_tol)

@@ -23,6 +23,7 @@ class Params(ct.Structure):
         ("periodic", ct.c_int * 3),
         ("reservoir_z", ct.c_int),
         ("rho_in", ct.c_double), ("rho_out", ct.c_double),
+        ("flux_in", ct.c_double),
     ]
 
 

@@ -84,6 +84,10 @@ void free_image(lbpm_ctx* c) {
     dfree(c, c->d_halo_site);
     dfree(c, c->d_slab_site);
     dfree(c, c->d_slab_side);
+    dfree(c, c->d_face_part);
+    dfree(c, c->d_face_rho);
+    c->d_face_part = nullptr;
+    c->d_face_rho = nullptr;
     c->d_labels = nullptr;
     c->d_site_vox = c->d_vsite = c->d_halo_dst = c->d_halo_site = c->d_slab_site = nullptr;
     c->d_phi = nullptr;
@@ -155,12 +159,17 @@ lbpm_status build_boundaries(lbpm_ctx* c) {
     dfree(c, scan);
     if (e != cudaSuccess) return fail_cuda(c, "halo construction", e);
 
-    // reservoir slabs
+    // reservoir slabs / boundary faces
     dfree(c, c->d_slab_site);
     dfree(c, c->d_slab_side);
     c->d_slab_site = nullptr;
     c->d_slab_side = nullptr;
     c->n_slab = 0;
+    if (c->params.reservoir_z == 3 && !c->d_face_part) {
+        c->d_face_part = static_cast<double*>(dalloc(c, sizeof(double) * 2 * kFaceBlocks));
+        c->d_face_rho = static_cast<float*>(dalloc(c, sizeof(float) * 2));
+        if (!c->d_face_part || !c->d_face_rho) return fail(c, LBPM_E_OOM, "device allocation of the flux inlet failed");
+    }
     if (c->params.reservoir_z) {
         LBPM_ALLOC(c, flags, int, c->N);
         scan = static_cast<int*>(dalloc(c, sizeof(int) * c->N));
@@ -202,10 +211,12 @@ lbpm_status check_params(lbpm_ctx* c, const lbpm_params* p) {
     }
     if (p->precision != LBPM_FP32 && p->precision != LBPM_FP16)
         return fail(c, LBPM_E_INVALID, "precision must be LBPM_FP32 or LBPM_FP16");
-    if (p->reservoir_z < 0 || p->reservoir_z > 2) return fail(c, LBPM_E_INVALID, "reservoir_z must be 0, 1 or 2");
-    if (p->reservoir_z == 2 && !(p->rho_in > 0.0 && p->rho_out > 0.0 && std::isfinite(p->rho_in) &&
+    if (p->reservoir_z < 0 || p->reservoir_z > 3) return fail(c, LBPM_E_INVALID, "reservoir_z must be 0, 1, 2 or 3");
+    if (p->reservoir_z >= 2 && !(p->rho_in > 0.0 && p->rho_out > 0.0 && std::isfinite(p->rho_in) &&
                                  std::isfinite(p->rho_out)))
         return fail(c, LBPM_E_INVALID, "the pressure boundary needs finite rho_in, rho_out > 0");
+    if (p->reservoir_z == 3 && !(p->flux_in >= 0.0 && std::isfinite(p->flux_in)))
+        return fail(c, LBPM_E_INVALID, "the flux inlet needs a finite flux_in >= 0");
     if (p->reservoir_z && p->periodic[2]) return fail(c, LBPM_E_INVALID, "reservoirs need a non-periodic z axis");
     if (!(p->rho_in > 0.0) || !(p->rho_out > 0.0)) return fail(c, LBPM_E_INVALID, "rho_in and rho_out must be > 0");
     return LBPM_OK;

@@ -299,8 +299,8 @@ cudaError_t launch_affinity_map(const lbpm_ctx* c, const float* map, cudaStream_
     return cudaGetLastError();
 }
 
-// reservoir slabs are four layers deep; the pressure boundary acts on the face layer
-int slab_depth(const lbpm_ctx* c) { return c->params.reservoir_z == 2 ? 1 : 4; }
+// reservoir slabs are four layers deep; the pressure and flux boundaries act on the face layer
+int slab_depth(const lbpm_ctx* c) { return c->params.reservoir_z >= 2 ? 1 : 4; }
 
 cudaError_t launch_slab_flags(const lbpm_ctx* c, int* flags, cudaStream_t s) {
     k_slab_flags<<<blocks_for(c->N), kBlock, 0, s>>>(c->d_site_vox, c->N, c->px * c->py, c->nz, slab_depth(c),

@@ -77,6 +77,8 @@ struct lbpm_ctx {
     int* d_halo_site = nullptr;     // [H]
     float* d_nsum = nullptr;        // [N] fp32 store
     float2* d_nab[2] = {nullptr, nullptr};  // [N] each, fp16 store
+    double* d_face_part = nullptr;          // flux inlet: per-block sums (2 * kFaceBlocks)
+    float* d_face_rho = nullptr;            // flux inlet: (rho, rho - 1) of the inlet face
     float* d_drho = nullptr;                // [N] fp16 store
     void* d_f = nullptr;
     void* d_a = nullptr;
@@ -126,6 +128,8 @@ cudaError_t launch_init_fluids(const lbpm_ctx* c, const float* phi0, cudaStream_
 cudaError_t launch_phase(const lbpm_ctx* c, int parity, cudaStream_t s);
 cudaError_t launch_collide(const lbpm_ctx* c, int parity, cudaStream_t s);
 cudaError_t launch_reservoir(const lbpm_ctx* c, int parity, cudaStream_t s);
+// flux inlet: blocks of the fixed-order face reduction
+constexpr int kFaceBlocks = 64;
 cudaError_t launch_morph(const lbpm_ctx* c, int parity, float delta, int R, int apply, float* phi_grid,
                          float* dist_grid, float* ntot, int3* off, long long* off_lin, float* off_len, int n_off,
                          unsigned long long* counts, cudaStream_t s);

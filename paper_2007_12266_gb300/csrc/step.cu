@@ -45,9 +45,53 @@ template <int PAR, class S>
 __global__ void __launch_bounds__(kBlock) k_pressure_faces(DomainView d, const int* sites,
                                                            const signed char* side, int n_face,
                                                            float rho_in, float rho_out, float drho_in,
-                                                           float drho_out) {
+                                                           float drho_out, const float* face) {
     const int i = blockIdx.x * kBlock + threadIdx.x;
-    if (i < n_face) pressure_face_thread<PAR, S>(d, sites[i], side[i], rho_in, rho_out, drho_in, drho_out);
+    if (i < n_face) pressure_face_thread<PAR, S>(d, sites[i], side[i], rho_in, rho_out, drho_in, drho_out, face);
+}
+
+// Flux inlet, first half: per-block sums (fixed grid, fixed order: the result
+// does not depend on scheduling) of D_s over the inlet sites and their count.
+template <int PAR, class S>
+__global__ void __launch_bounds__(kBlock) k_face_sum(DomainView d, const int* sites, const signed char* side,
+                                                     int n_face, double* part) {
+    __shared__ double sd[kBlock];
+    __shared__ double sc[kBlock];
+    double acc = 0.0, cnt = 0.0;
+    for (int i = blockIdx.x * kBlock + threadIdx.x; i < n_face; i += kFaceBlocks * kBlock) {
+        if (side[i] != 1) continue;
+        int nb[Q19];
+        float dv[Q19], nx, ny;
+        acc += face_deviations<PAR, S>(d, sites[i], 1.0f, nb, dv, nx, ny);
+        cnt += 1.0;
+    }
+    sd[threadIdx.x] = acc;
+    sc[threadIdx.x] = cnt;
+    __syncthreads();
+    for (int w = kBlock / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) {
+            sd[threadIdx.x] += sd[threadIdx.x + w];
+            sc[threadIdx.x] += sc[threadIdx.x + w];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        part[2 * blockIdx.x] = sd[0];
+        part[2 * blockIdx.x + 1] = sc[0];
+    }
+}
+
+// Second half: rho_in - 1 = (sum D + Q) / (n_in - Q), from sum_s (1 + D_s) / (n_in - Q).
+__global__ void k_face_rho(const double* part, double flux, float* face) {
+    if (threadIdx.x != 0) return;
+    double D = 0.0, n = 0.0;
+    for (int b = 0; b < kFaceBlocks; ++b) {
+        D += part[2 * b];
+        n += part[2 * b + 1];
+    }
+    const double drho = n > flux ? (D + flux) / (n - flux) : 0.0;
+    face[0] = static_cast<float>(1.0 + drho);
+    face[1] = static_cast<float>(drho);
 }
 
 template <int PAR, class S>
@@ -195,17 +239,30 @@ cudaError_t launch_reservoir(const lbpm_ctx* c, int parity, cudaStream_t s) {
     const int ns = static_cast<int>(c->n_slab);
     const float ri = static_cast<float>(c->params.rho_in), ro = static_cast<float>(c->params.rho_out);
     const bool h = c->params.precision == LBPM_FP16;
-    if (c->params.reservoir_z == 2) {   // pressure boundary at the z faces
+    if (c->params.reservoir_z >= 2) {   // pressure faces; flux inlet (3)
         // rho - 1 formed in double, so the small difference keeps full fp32 precision
         const float di = static_cast<float>(c->params.rho_in - 1.0), dout = static_cast<float>(c->params.rho_out - 1.0);
         const int* st = c->d_slab_site;
         const signed char* sd = c->d_slab_side;
+        float* face = nullptr;
+        if (c->params.reservoir_z == 3) {
+            face = c->d_face_rho;
+            double* part = c->d_face_part;
+            if (parity == 0) {
+                if (h) k_face_sum<0, StoreF16><<<kFaceBlocks, kBlock, 0, s>>>(d, st, sd, ns, part);
+                else k_face_sum<0, StoreF32><<<kFaceBlocks, kBlock, 0, s>>>(d, st, sd, ns, part);
+            } else {
+                if (h) k_face_sum<1, StoreF16><<<kFaceBlocks, kBlock, 0, s>>>(d, st, sd, ns, part);
+                else k_face_sum<1, StoreF32><<<kFaceBlocks, kBlock, 0, s>>>(d, st, sd, ns, part);
+            }
+            k_face_rho<<<1, 32, 0, s>>>(part, c->params.flux_in, face);
+        }
         if (parity == 0) {
-            if (h) k_pressure_faces<0, StoreF16><<<g, kBlock, 0, s>>>(d, st, sd, ns, ri, ro, di, dout);
-            else k_pressure_faces<0, StoreF32><<<g, kBlock, 0, s>>>(d, st, sd, ns, ri, ro, di, dout);
+            if (h) k_pressure_faces<0, StoreF16><<<g, kBlock, 0, s>>>(d, st, sd, ns, ri, ro, di, dout, face);
+            else k_pressure_faces<0, StoreF32><<<g, kBlock, 0, s>>>(d, st, sd, ns, ri, ro, di, dout, face);
         } else {
-            if (h) k_pressure_faces<1, StoreF16><<<g, kBlock, 0, s>>>(d, st, sd, ns, ri, ro, di, dout);
-            else k_pressure_faces<1, StoreF32><<<g, kBlock, 0, s>>>(d, st, sd, ns, ri, ro, di, dout);
+            if (h) k_pressure_faces<1, StoreF16><<<g, kBlock, 0, s>>>(d, st, sd, ns, ri, ro, di, dout, face);
+            else k_pressure_faces<1, StoreF32><<<g, kBlock, 0, s>>>(d, st, sd, ns, ri, ro, di, dout, face);
         }
         return cudaGetLastError();
     }

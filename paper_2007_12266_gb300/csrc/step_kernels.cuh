@@ -595,30 +595,28 @@ __device__ __forceinline__ void reservoir_thread(const DomainView& d, int n, int
 // B = 0; outlet B = w rho_out (1 - 4.5 u_z), A = 0. The values go into the
 // slots the NEXT step (parity PAR) reads.
 // ---------------------------------------------------------------------------
+// Incoming populations of the next step at face site n as deviations
+// d_q = f_q - t_q, and D = S_0 + 2 S_out - 1 in deviations (the weights of
+// S_0 + 2 S_out add up to one): u_n is then formed from small numbers and
+// rho - 1 instead of cancelling O(1) sums. nb: neighbour ids (filled here).
 template <int PAR, class S>
-__device__ __forceinline__ void pressure_face_thread(const DomainView& d, int n, int side, float rho_in,
-                                                     float rho_out, float drho_in, float drho_out) {
+__device__ __forceinline__ float face_deviations(const DomainView& d, int n, float sgn, int (&nb)[Q19],
+                                                 float (&dv)[Q19], float& nx, float& ny) {
     const int v = d.site_vox[n];
-    int nb[Q19];
     if constexpr (PAR == 1 || S::kRef) {
         static_for<1, Q19>([&](auto qc) {
             constexpr int q = decltype(qc)::value;
             nb[q] = __ldg(d.vsite + v + stencil_off(d, q));
         });
     }
-    // incoming populations of the next step as deviations d_q = f_q - t_q: the
-    // weights of the sums below add up to one, so u_n is formed from small
-    // numbers and rho - 1 (exact in fp32) instead of cancelling O(1) sums
-    float dv[Q19];
     static_for<0, Q19>([&](auto qc) {
         constexpr int q = decltype(qc)::value;
         dv[q] = S::template ld_fdev<q>(d.f, read_slot<PAR, q>(d, n, nb));
         if constexpr (S::kRef) dv[q] = fmaf(t19(q), d.drho[f_ref_read<PAR, q>(n, nb)], dv[q]);
     });
-    const float sgn = side == 1 ? 1.0f : -1.0f;       // face normal into the domain
-    const float rho = side == 1 ? rho_in : rho_out;
-    const float drho = side == 1 ? drho_in : drho_out;
-    float D = 0.0f, nx = 0.0f, ny = 0.0f;
+    float D = 0.0f;
+    nx = 0.0f;
+    ny = 0.0f;
     static_for<0, Q19>([&](auto qc) {
         constexpr int q = decltype(qc)::value;
         if constexpr (cz(q) == 0) {
@@ -629,6 +627,26 @@ __device__ __forceinline__ void pressure_face_thread(const DomainView& d, int n,
             if (cz(q) * sgn < 0.0f) D += 2.0f * dv[q];   // leaving the domain through this face
         }
     });
+    return D;
+}
+
+// face: (rho, rho - 1) of the inlet computed on the device (flux inlet), or
+// nullptr to take rho_in, drho_in
+template <int PAR, class S>
+__device__ __forceinline__ void pressure_face_thread(const DomainView& d, int n, int side, float rho_in,
+                                                     float rho_out, float drho_in, float drho_out,
+                                                     const float* face) {
+    if (face && side == 1) {
+        rho_in = face[0];
+        drho_in = face[1];
+    }
+    int nb[Q19];
+    float dv[Q19];
+    const float sgn = side == 1 ? 1.0f : -1.0f;       // face normal into the domain
+    const float rho = side == 1 ? rho_in : rho_out;
+    const float drho = side == 1 ? drho_in : drho_out;
+    float nx, ny;
+    const float D = face_deviations<PAR, S>(d, n, sgn, nb, dv, nx, ny);
     nx *= 0.5f;
     ny *= 0.5f;
     const float un = (drho - D) / rho;                // velocity along the inward normal

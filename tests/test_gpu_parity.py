@@ -206,15 +206,15 @@ def test_reservoir_slabs_parity():
     assert mo["sat_mass"] > 0.05     # fluid A entered from the inlet
 
 
-@pytest.mark.parametrize("precision", ["fp32", "fp16"])
-def test_pressure_faces_parity(precision):
-    """Pressure boundary at the z faces (reservoir_z = 2) against the oracle:
-    every distribution over the first steps (fp32), then saturation and the
-    Darcy flux after 200 steps."""
+@pytest.mark.parametrize("precision,mode", [("fp32", 2), ("fp16", 2), ("fp32", 3), ("fp16", 3)])
+def test_pressure_faces_parity(precision, mode):
+    """Pressure boundary at the z faces (reservoir_z = 2) and flux inlet
+    (reservoir_z = 3) against the oracle: every distribution over the first
+    steps (fp32), then saturation and the Darcy flux after 200 steps."""
     sp = sphere_pack((12, 10, 24), 0.55, 2.0, 0.5, 19)
     lab = sp.labels
     aff = uniform_affinity(lab, -0.7)
-    kw = dict(KW, reservoir_z=2, rho_in=1.002, rho_out=0.998)
+    kw = dict(KW, reservoir_z=mode, rho_in=1.002, rho_out=0.998, flux_in=0.2)
     per = (1, 1, 0)
     dom, ref = pair(lab, aff, per, precision=precision, **kw)
     phi0 = np.full(lab.shape, -1.0, np.float32)

@@ -1,5 +1,6 @@
 """Pins of the oracle's pressure boundary at the z faces (reservoir_z = 2;
-Sec. 4.1 cites Zou and He's constant-pressure scheme).
+Sec. 4.1 cites Zou and He's constant-pressure scheme) and of the flux inlet
+(reservoir_z = 3; Sec. 4.1's flux condition: a total volumetric flow rate).
 
 * Construction: after every step each face site holds exactly the face
   density and no tangential momentum.
@@ -15,7 +16,7 @@ import pytest
 import oracle
 from test_oracle_physics import duct_series
 
-def _duct(a, nz, rin, rout, tau=0.7):
+def _duct(a, nz, rin, rout, tau=0.7, mode=2, flux=0.0):
     n = a + 2
     lab = np.ones((nz, n, n), np.uint16)
     lab[:, 1:-1, 1:-1] = 0
@@ -23,7 +24,7 @@ def _duct(a, nz, rin, rout, tau=0.7):
     # alpha = 0 and tau_a = tau_b: the momentum equation is single phase
     # whatever the two components do
     o = oracle.Oracle(lab, aff, (0, 0, 0), tau_a=tau, tau_b=tau, alpha=0.0, beta=0.95, force=(0, 0, 0),
-                      reservoir_z=2, rho_in=rin, rho_out=rout)
+                      reservoir_z=mode, rho_in=rin, rho_out=rout, flux_in=flux)
     o.init_fluids(np.ones(lab.shape, np.float32))
     return o, lab
 
@@ -63,3 +64,40 @@ def test_pressure_driven_duct_matches_the_body_force_series():
     rho = 3.0 * o.dense(p)
     flux = np.nansum((rho * uz)[:, 1:-1, 1:-1], axis=(1, 2))
     assert np.abs(flux / flux[nz // 2] - 1).max() < 2e-3
+
+
+def test_flux_inlet_carries_exactly_the_prescribed_flux():
+    a, nz, Q = 6, 12, 0.3
+    o, lab = _duct(a, nz, 1.0, 0.999, mode=3, flux=Q)
+    xi = oracle.lattice_tables()[0]
+    sv, _ = o.index()
+    inlet = sv // (lab.shape[1] * lab.shape[2]) == 0
+    for _ in range(5):
+        o.step(3)
+        f, _, _ = o.state()
+        rho = f[:, inlet].sum(axis=0)
+        uz = (xi[:, 2] @ f[:, inlet]) / rho
+        assert abs(uz.sum() - Q) < 1e-12
+        assert np.abs(rho - rho[0]).max() < 1e-14        # one uniform inlet density
+        assert np.abs(xi[:, 0] @ f[:, inlet]).max() < 1e-14
+
+
+def test_flux_driven_duct_has_the_poiseuille_profile_and_flux():
+    a, nz, Q = 16, 48, 0.4
+    o, lab = _duct(a, nz, 1.0, 1.0, mode=3, flux=Q)
+    o.step(4000)
+    _, p, u = o.fields()
+    uz = o.dense(u[2])
+    rho = 3.0 * o.dense(p)
+    mid = uz[nz // 2, 1:-1, 1:-1]
+    # the steady mass flux of every section is the inlet's: rho_in Q
+    flux = np.nansum((rho * uz)[:, 1:-1, 1:-1], axis=(1, 2))
+    assert np.abs(flux / flux[nz // 2] - 1).max() < 2e-3
+    assert abs(mid.sum() / Q - 1) < 5e-3
+    # the profile is the duct series, scaled to the same total
+    n = a + 2
+    c = np.arange(1, n - 1) - (n - 1) / 2
+    yy, xx = np.meshgrid(c, c, indexing="ij")
+    shape = duct_series(a, 1.0, 1.0, xx, yy)
+    shape *= mid.sum() / shape.sum()
+    assert np.abs(mid - shape).max() < 3e-3 * shape.max()
