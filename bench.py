@@ -50,6 +50,26 @@ def dist_env():
         int(os.environ.get("WORLD_SIZE", 1))
 
 
+def shard(n_items: int, rank: int, world: int):
+    """Indices of the independent units (jobs) rank `rank` of `world` runs:
+    round-robin, every unit on exactly one rank, no data exchange."""
+    return list(range(rank, n_items, world))
+
+
+def reduce_over_ranks(ms: float, units: float, world: int, device="cpu"):
+    """(max over ranks of the timed milliseconds, sum over ranks of the units
+    processed): the job's time is its slowest rank's."""
+    if world <= 1:
+        return ms, units
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    u = torch.tensor([units], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -532,11 +552,7 @@ def bench_gpu(args):
     launches = dom.launch_count - l0
     clocks = sampler.stop()
     ms = ev0.elapsed_time(ev1)
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    site_updates = N * bundle * args.steps * world
+    ms, site_updates = reduce_over_ranks(ms, float(N * bundle * args.steps), world, dev)
     value = site_updates / (ms * 1e-3) / 1e6
 
     # per-kernel durations: a second pass with CUDA events around every launch
@@ -599,12 +615,19 @@ def bench_gpu(args):
                 "sat_mass": m16["sat_mass"], "flux_z": m16["flux"][2]}
 
     batched = None
-    if not args.no_batched and world == 1:
+    if not args.no_batched:
         try:
-            jobs = _spawn_map(_batched_job, list(range(args.batched_jobs)))
-            batched = {"workload": f"{len(jobs)} sphere-pack jobs, L in {{64..192}}, porosity U[0.15,0.35]",
-                       "fp32": bench_batched(jobs, "fp32", args.batched_steps, local_rank),
-                       "fp16": bench_batched(jobs, "fp16", args.batched_steps, local_rank)}
+            # the jobs are independent: each rank runs its round-robin share
+            mine = shard(args.batched_jobs, rank, world)
+            jobs = _spawn_map(_batched_job, mine)
+            batched = {"workload": f"{args.batched_jobs} sphere-pack jobs, L in {{64..192}}, porosity U[0.15,0.35]"
+                                   + (f", {world} ranks, round-robin shards" if world > 1 else "")}
+            for prec in ("fp32", "fp16"):
+                r = bench_batched(jobs, prec, args.batched_steps, local_rank)
+                ms_all, su_all = reduce_over_ranks(r["ms"], float(r["n_sites"] * r["steps"]), world, dev)
+                r["value"] = su_all / (ms_all * 1e-3) / 1e6
+                r["ms"] = ms_all
+                batched[prec] = r
             batched["fp16_vs_fp32"] = batched["fp16"]["value"] / batched["fp32"]["value"]
             batched["fp16_vs_plain_fp32"] = batched["fp16"]["value"] / value
             del jobs
