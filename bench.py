@@ -622,12 +622,12 @@ def bench_gpu(args):
             jobs = _spawn_map(_batched_job, mine)
             batched = {"workload": f"{args.batched_jobs} sphere-pack jobs, L in {{64..192}}, porosity U[0.15,0.35]"
                                    + (f", {world} ranks, round-robin shards" if world > 1 else "")}
-            for prec in ("fp32", "fp16"):
-                r = bench_batched(jobs, prec, args.batched_steps, local_rank)
+            for bprec in ("fp32", "fp16"):
+                r = bench_batched(jobs, bprec, args.batched_steps, local_rank)
                 ms_all, su_all = reduce_over_ranks(r["ms"], float(r["n_sites"] * r["steps"]), world, dev)
                 r["value"] = su_all / (ms_all * 1e-3) / 1e6
                 r["ms"] = ms_all
-                batched[prec] = r
+                batched[bprec] = r
             batched["fp16_vs_fp32"] = batched["fp16"]["value"] / batched["fp32"]["value"]
             batched["fp16_vs_plain_fp32"] = batched["fp16"]["value"] / value
             del jobs
