@@ -64,13 +64,12 @@ void free_state(lbpm_ctx* c) {
     dfree(c, c->d_a);
     dfree(c, c->d_b);
     dfree(c, c->d_nsum);
-    dfree(c, c->d_nab[0]);
-    dfree(c, c->d_nab[1]);
     dfree(c, c->d_drho);
+    dfree(c, c->d_phi_alt);
     c->d_drho = nullptr;
+    c->d_phi_alt = nullptr;
     c->d_f = c->d_a = c->d_b = nullptr;
     c->d_nsum = nullptr;
-    c->d_nab[0] = c->d_nab[1] = nullptr;
     c->have_fluids = false;
 }
 
@@ -82,6 +81,8 @@ void free_image(lbpm_ctx* c) {
     dfree(c, c->d_phi);
     dfree(c, c->d_halo_dst);
     dfree(c, c->d_halo_site);
+    dfree(c, c->d_wall6);
+    c->d_wall6 = nullptr;
     dfree(c, c->d_slab_site);
     dfree(c, c->d_slab_side);
     dfree(c, c->d_face_part);
@@ -106,15 +107,17 @@ lbpm_status alloc_state(lbpm_ctx* c) {
     c->d_f = dalloc(c, state_bytes(c, 19));
     c->d_a = dalloc(c, state_bytes(c, 7));
     c->d_b = dalloc(c, state_bytes(c, 7));
-    bool ok = c->d_f && c->d_a && c->d_b;
+    c->d_nsum = static_cast<float*>(dalloc(c, sizeof(float) * c->N));
+    bool ok = c->d_f && c->d_a && c->d_b && c->d_nsum;
     if (c->params.precision == LBPM_FP16) {
-        c->d_nab[0] = static_cast<float2*>(dalloc(c, sizeof(float2) * c->N));
-        c->d_nab[1] = static_cast<float2*>(dalloc(c, sizeof(float2) * c->N));
+        // the second phase grid starts as a copy of the first (solids, walls
+        // and their periodic mirrors are static and the same in both)
         c->d_drho = static_cast<float*>(dalloc(c, sizeof(float) * c->N));
-        ok = ok && c->d_nab[0] && c->d_nab[1] && c->d_drho;
-    } else {
-        c->d_nsum = static_cast<float*>(dalloc(c, sizeof(float) * c->N));
-        ok = ok && c->d_nsum;
+        c->d_phi_alt = static_cast<float*>(dalloc(c, sizeof(float) * c->Vp));
+        ok = ok && c->d_drho && c->d_phi_alt;
+        if (ok && cudaMemcpyAsync(c->d_phi_alt, c->d_phi, sizeof(float) * c->Vp, cudaMemcpyDeviceToDevice,
+                                  c->stream) != cudaSuccess)
+            ok = false;
     }
     if (!ok) {
         free_state(c);
@@ -154,6 +157,11 @@ lbpm_status build_boundaries(lbpm_ctx* c) {
             else e = launch_halo_scatter(c, flags, scan, c->stream);
         }
     }
+    if (e == cudaSuccess && !c->d_wall6) {
+        c->d_wall6 = static_cast<unsigned char*>(dalloc(c, c->N));
+        if (!c->d_wall6) e = cudaErrorMemoryAllocation;
+    }
+    if (e == cudaSuccess) e = launch_wall_mask(c, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     dfree(c, flags);
     dfree(c, scan);
@@ -538,7 +546,7 @@ lbpm_status lbpm_init_fluids(lbpm_ctx* c, const float* phi0) {
     c->step = 0;
     c->have_fluids = true;
     c->unstable = false;
-    c->launches += 2;
+    c->launches += c->params.precision == LBPM_FP16 ? 4 : 2;
     return LBPM_OK;
 }
 

@@ -146,7 +146,8 @@ Geo geo_of(const lbpm_ctx* c) {
                c->params.periodic[2], c->Vp};
 }
 
-__global__ void k_fill_halo(Geo g, int* vsite, float* phi) {
+// phi2: the second phase grid (fp16 storage), or nullptr
+__global__ void k_fill_halo(Geo g, int* vsite, float* phi, float* phi2) {
     const long long pv = static_cast<long long>(blockIdx.x) * kBlock + threadIdx.x;
     if (pv >= g.Vp) return;
     long long src = 0;
@@ -154,9 +155,11 @@ __global__ void k_fill_halo(Geo g, int* vsite, float* phi) {
     if (k == 1) {
         vsite[pv] = vsite[src];
         phi[pv] = phi[src];
+        if (phi2) phi2[pv] = phi2[src];
     } else if (k == 2) {
         vsite[pv] = -1;
         phi[pv] = 0.0f;
+        if (phi2) phi2[pv] = 0.0f;
     }
 }
 
@@ -178,20 +181,25 @@ __global__ void k_halo_scatter(long long Vp, const int* flags, const int* scan, 
 }
 
 __global__ void k_affinity_table(const uint16_t* labels, long long V, int nx, int ny, int px, int py,
-                                 const float* table, int n_labels, float* phi) {
+                                 const float* table, int n_labels, float* phi, float* phi2) {
     const long long v = static_cast<long long>(blockIdx.x) * kBlock + threadIdx.x;
     if (v >= V) return;
     const int lab = labels[v];
     if (lab == 0) return;
-    phi[padded_of(v, nx, ny, px, py)] = lab < n_labels ? table[lab] : 0.0f;
+    const float a = lab < n_labels ? table[lab] : 0.0f;
+    const long long pv = padded_of(v, nx, ny, px, py);
+    phi[pv] = a;
+    if (phi2) phi2[pv] = a;
 }
 
 __global__ void k_affinity_map(const uint16_t* labels, long long V, int nx, int ny, int px, int py,
-                               const float* map, float* phi) {
+                               const float* map, float* phi, float* phi2) {
     const long long v = static_cast<long long>(blockIdx.x) * kBlock + threadIdx.x;
     if (v >= V) return;
     if (labels[v] == 0) return;
-    phi[padded_of(v, nx, ny, px, py)] = map[v];
+    const long long pv = padded_of(v, nx, ny, px, py);
+    phi[pv] = map[v];
+    if (phi2) phi2[pv] = map[v];
 }
 
 // 1: inlet (the first `depth` z layers), 2: outlet (the last ones), 0: neither
@@ -229,6 +237,20 @@ __global__ void k_export_index(const int* site_vox, const int* vsite, long long 
     if (nbr) {
         for (int q = 1; q < Q19; ++q) nbr[static_cast<long long>(q - 1) * N + n] = vsite[pv + stencil_off(d, q)];
     }
+}
+
+// Which face links of each site bounce back: bit q - 1 for x + xi_q solid or
+// wall (q = 1..6). Read by the fp16 collision to pick the site whose phase is
+// the reference of each stored component value.
+__global__ void k_wall_mask(const int* site_vox, const int* vsite, long long N, int px, int pxpy,
+                            unsigned char* wall6) {
+    const long long n = static_cast<long long>(blockIdx.x) * kBlock + threadIdx.x;
+    if (n >= N) return;
+    const int pv = site_vox[n];
+    unsigned m = 0;
+    for (int q = 1; q < Q7; ++q)
+        if (vsite[pv + stencil_offset(q, px, pxpy)] < 0) m |= 1u << (q - 1);
+    wall6[n] = static_cast<unsigned char>(m);
 }
 
 }  // namespace
@@ -272,7 +294,7 @@ cudaError_t launch_scatter_sites(const lbpm_ctx* c, const int* scan, cudaStream_
 }
 
 cudaError_t launch_fill_halo(const lbpm_ctx* c, cudaStream_t s) {
-    k_fill_halo<<<blocks_for(c->Vp), kBlock, 0, s>>>(geo_of(c), c->d_vsite, c->d_phi);
+    k_fill_halo<<<blocks_for(c->Vp), kBlock, 0, s>>>(geo_of(c), c->d_vsite, c->d_phi, c->d_phi_alt);
     return cudaGetLastError();
 }
 
@@ -289,13 +311,13 @@ cudaError_t launch_halo_scatter(const lbpm_ctx* c, const int* flags, const int* 
 
 cudaError_t launch_affinity_table(const lbpm_ctx* c, const float* table, int n_labels, cudaStream_t s) {
     k_affinity_table<<<blocks_for(c->V), kBlock, 0, s>>>(c->d_labels, c->V, c->nx, c->ny, c->px, c->py,
-                                                         table, n_labels, c->d_phi);
+                                                         table, n_labels, c->d_phi, c->d_phi_alt);
     return cudaGetLastError();
 }
 
 cudaError_t launch_affinity_map(const lbpm_ctx* c, const float* map, cudaStream_t s) {
     k_affinity_map<<<blocks_for(c->V), kBlock, 0, s>>>(c->d_labels, c->V, c->nx, c->ny, c->px, c->py,
-                                                       map, c->d_phi);
+                                                       map, c->d_phi, c->d_phi_alt);
     return cudaGetLastError();
 }
 
@@ -318,6 +340,13 @@ cudaError_t launch_export_index(const lbpm_ctx* c, long long* site2vox, int* nbr
     if (c->N == 0) return cudaSuccess;
     k_export_index<<<blocks_for(c->N), kBlock, 0, s>>>(c->d_site_vox, c->d_vsite, c->N, c->nx, c->ny,
                                                        c->px, c->py, make_view(c), site2vox, nbr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_wall_mask(const lbpm_ctx* c, cudaStream_t s) {
+    if (c->N == 0) return cudaSuccess;
+    k_wall_mask<<<blocks_for(c->N), kBlock, 0, s>>>(c->d_site_vox, c->d_vsite, c->N, c->px,
+                                                    c->px * c->py, c->d_wall6);
     return cudaGetLastError();
 }
 

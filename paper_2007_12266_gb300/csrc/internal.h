@@ -23,12 +23,15 @@ struct DomainView {
     int px, pxpy;       // padded-grid strides in y and z: xi_q is at offset cx + cy px + cz pxpy
     const int* site_vox;   // [N] padded voxel of each site
     const int* vsite;      // [Vp] site id, -1 for solid / wall
-    float* phi;            // [Vp] phase field; solids hold phi_s, walls 0
+    float* phi[2];         // [Vp] phase field by step parity: the phase pass of a step of parity P
+                           //     writes phi[P] and the collision reads it; with fp16 storage the
+                           //     previous step's phi[P ^ 1] is the reference of the stored
+                           //     components (with fp32 storage both point to one grid).
+                           //     Solids hold phi_s, walls 0.
     const int* halo_dst;   // [H] padded halo voxel
     const int* halo_site;  // [H] site it mirrors
-    float* nsum;           // [N] Na + Nb of the current step (phase pass -> collision), fp32 store
-    float2* nab[2];        // [N] (Na, Nb) per site by step parity, fp16 store: the reference of the
-                           //     stored component deviations and the phase pass -> collision hand-off
+    const unsigned char* wall6;  // [N] bit q - 1 set when x + xi_q (q = 1..6) is solid or wall
+    float* nsum;           // [N] Na + Nb of the current step (phase pass -> collision)
     float* drho;           // [N] rho - 1 of each site at the last even step, fp16 store: the
                            //     reference of the stored momentum deviations
     void* f;               // [19][N] momentum distributions (AA in place)
@@ -73,10 +76,11 @@ struct lbpm_ctx {
     int* d_site_vox = nullptr;      // [N]
     int* d_vsite = nullptr;         // [Vp]
     float* d_phi = nullptr;         // [Vp]
+    float* d_phi_alt = nullptr;     // [Vp] fp16 storage: the phase grid of odd steps
     int* d_halo_dst = nullptr;      // [H]
     int* d_halo_site = nullptr;     // [H]
-    float* d_nsum = nullptr;        // [N] fp32 store
-    float2* d_nab[2] = {nullptr, nullptr};  // [N] each, fp16 store
+    unsigned char* d_wall6 = nullptr;  // [N] face links that bounce back
+    float* d_nsum = nullptr;        // [N]
     double* d_face_part = nullptr;          // flux inlet: per-block sums (2 * kFaceBlocks)
     float* d_face_rho = nullptr;            // flux inlet: (rho, rho - 1) of the inlet face
     float* d_drho = nullptr;                // [N] fp16 store
@@ -122,6 +126,7 @@ cudaError_t launch_affinity_map(const lbpm_ctx* c, const float* map, cudaStream_
 cudaError_t launch_slab_flags(const lbpm_ctx* c, int* flags, cudaStream_t s);
 cudaError_t launch_slab_scatter(const lbpm_ctx* c, const int* flags, const int* scan, cudaStream_t s);
 cudaError_t launch_export_index(const lbpm_ctx* c, long long* site2vox, int* nbr, cudaStream_t s);
+cudaError_t launch_wall_mask(const lbpm_ctx* c, cudaStream_t s);
 
 DomainView make_view(const lbpm_ctx* c);
 cudaError_t launch_init_fluids(const lbpm_ctx* c, const float* phi0, cudaStream_t s);

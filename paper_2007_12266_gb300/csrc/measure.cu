@@ -96,26 +96,18 @@ __global__ void __launch_bounds__(kBlock) k_export(DomainView d, int which, floa
     }
 }
 
-// fp16 store: the reference densities of imported component populations are
-// the sums of the imported values at each site (any reference works as long
-// as the reader uses the same one).
-template <int PAR>
-__global__ void __launch_bounds__(kBlock) k_import_ref(DomainView d, int which, const float* in) {
+// fp16 store: the reference density of imported momentum populations is the
+// sum of the imported values at each site (any reference works as long as the
+// reader uses the same one); imported component values are stored relative to
+// the references the next step reads them with (the previous phase grid).
+__global__ void __launch_bounds__(kBlock) k_import_ref(DomainView d, const float* in) {
     const int n = blockIdx.x * kBlock + threadIdx.x;
     if (n >= d.n_sites) return;
     const size_t N = d.n_sites;
     float s = 0.0f;
-    if (which == LBPM_DIST_F) {
 #pragma unroll
-        for (int q = 0; q < Q19; ++q) s += in[q * N + n];
-        d.drho[n] = s - 1.0f;
-        return;
-    }
-#pragma unroll
-    for (int q = 0; q < Q7; ++q) s += in[q * N + n];
-    float2* ref = d.nab[PAR ^ 1] + n;
-    if (which == LBPM_DIST_A) ref->x = s;
-    else ref->y = s;
+    for (int q = 0; q < Q19; ++q) s += in[q * N + n];
+    d.drho[n] = s - 1.0f;
 }
 
 template <int PAR, class S>
@@ -124,12 +116,13 @@ __global__ void __launch_bounds__(kBlock) k_import(DomainView d, int which, cons
     if (n >= d.n_sites) return;
     const int v = d.site_vox[n];
     int nb[Q19];
-    if constexpr (PAR == 1 || S::kRef) {
+    if constexpr (PAR == 1) {
         static_for<1, Q19>([&](auto qc) {
             constexpr int q = decltype(qc)::value;
             nb[q] = __ldg(d.vsite + v + stencil_off(d, q));
         });
     }
+    const unsigned wall = S::kRef ? __ldg(d.wall6 + n) : 0u;
     const size_t N = d.n_sites;
     static_for<0, Q19>([&](auto qc) {
         constexpr int q = decltype(qc)::value;
@@ -143,8 +136,8 @@ __global__ void __launch_bounds__(kBlock) k_import(DomainView d, int which, cons
             if (which != LBPM_DIST_F) {
                 float val = in[q * N + n];
                 if constexpr (S::kRef) {
-                    const float2 r = d.nab[PAR ^ 1][writer_of<q>(n, nb)];
-                    val -= w7(q) * (which == LBPM_DIST_A ? r.x : r.y);
+                    const float pw = writer_phase<PAR, q>(d, v, wall);
+                    val -= w7(q) * 0.5f * (which == LBPM_DIST_A ? 1.0f + pw : 1.0f - pw);
                 }
                 if (which == LBPM_DIST_A) S::template st_c<q>(d.a, i, val);
                 else S::template st_c<q>(d.b, i, val);
@@ -226,9 +219,8 @@ cudaError_t launch_export_dist(const lbpm_ctx* c, int parity, int which, float* 
 }
 
 cudaError_t launch_import_dist(const lbpm_ctx* c, int parity, int which, const float* in, cudaStream_t s) {
-    if (c->params.precision == LBPM_FP16 && c->N > 0) {
-        if (parity == 0) k_import_ref<0><<<blocks_for(c->N), kBlock, 0, s>>>(make_view(c), which, in);
-        else k_import_ref<1><<<blocks_for(c->N), kBlock, 0, s>>>(make_view(c), which, in);
+    if (c->params.precision == LBPM_FP16 && c->N > 0 && which == LBPM_DIST_F) {
+        k_import_ref<<<blocks_for(c->N), kBlock, 0, s>>>(make_view(c), in);
         const cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }

@@ -14,7 +14,7 @@ __device__ __forceinline__ void load_site(const DomainView& d, int n, float (&f)
                                           float (&b)[Q7]) {
     const int v = d.site_vox[n];
     int nb[Q19];
-    if constexpr (PAR == 1 || S::kRef) {
+    if constexpr (PAR == 1) {
         static_for<1, Q19>([&](auto qc) {
             constexpr int q = decltype(qc)::value;
             nb[q] = __ldg(d.vsite + v + stencil_off(d, q));
@@ -25,7 +25,7 @@ __device__ __forceinline__ void load_site(const DomainView& d, int n, float (&f)
         f[q] = S::template ld_f<q>(d.f, read_slot<PAR, q>(d, n, nb));
         if constexpr (S::kRef) f[q] = fmaf(t19(q), d.drho[f_ref_read<PAR, q>(n, nb)], f[q]);
     });
-    load_components<PAR, S>(d, n, nb, a, b);
+    load_components<PAR, S>(d, n, v, nb, a, b);
 }
 
 // Compensated fp32 accumulator (TwoSum): hi + lo carries about 48 bits, so a

@@ -124,20 +124,22 @@ __global__ void __launch_bounds__(kMorphBlock) k_morph_apply(DomainView d, Morph
             if (apply) {
                 const float N = g.ntot[n];
                 int nb[Q19];
-                if constexpr (PAR == 1 || S::kRef) {
+                if constexpr (PAR == 1) {
                     static_for<1, Q19>([&](auto qc) {
                         constexpr int q = decltype(qc)::value;
                         nb[q] = __ldg(d.vsite + v + stencil_off(d, q));
                     });
                 }
                 const float na = 0.5f * N * (1.0f + phin), nbb = 0.5f * N * (1.0f - phin);
+                const unsigned wall = S::kRef ? __ldg(d.wall6 + n) : 0u;
                 static_for<0, Q7>([&](auto qc) {
                     constexpr int q = decltype(qc)::value;
                     float av = w7(q) * na, bv = w7(q) * nbb;
                     if constexpr (S::kRef) {
-                        const float2 r = nab_prev<PAR>(d)[writer_of<q>(n, nb)];
-                        av -= w7(q) * r.x;
-                        bv -= w7(q) * r.y;
+                        // the reference the next step reads it with
+                        const float pw = writer_phase<PAR, q>(d, v, wall);
+                        av -= w7(q) * 0.5f * (1.0f + pw);
+                        bv -= w7(q) * 0.5f * (1.0f - pw);
                     }
                     const size_t i = read_slot<PAR, q>(d, n, nb);
                     S::template st_c<q>(d.a, i, av);

@@ -113,19 +113,19 @@ __device__ __forceinline__ float phi0_of_site(const DomainView& d, int n, const 
     return fminf(1.0f, fmaxf(-1.0f, p));
 }
 
-// fp16 store: densities of the initial state, as if written by a step -1 (the
-// reference of the deviations read at step 0).
-__global__ void __launch_bounds__(kBlock) k_init_ref(DomainView d, const float* phi0, int nx, int ny, int px,
-                                                     int pxpy) {
+// The phase grid that step 0 reads as the previous step's: phi0 (fp16
+// storage: the references of the initial component values).
+__global__ void __launch_bounds__(kBlock) k_init_phase(DomainView d, const float* phi0, int nx, int ny, int px,
+                                                       int pxpy) {
     const int n = blockIdx.x * kBlock + threadIdx.x;
     if (n >= d.n_sites) return;
-    const float p = phi0_of_site(d, n, phi0, nx, ny, px, pxpy);
-    d.nab[1][n] = make_float2(0.5f * (1.0f + p), 0.5f * (1.0f - p));
-    d.drho[n] = 0.0f;   // rho = 1
+    d.phi[1][d.site_vox[n]] = phi0_of_site(d, n, phi0, nx, ny, px, pxpy);
 }
 
 // Initial state consistent with phi0 (rho = 1, u = 0), written in the even
-// (natural) layout: Na = (1 + phi0)/2, Nb = (1 - phi0)/2.
+// (natural) layout: Na = (1 + phi0)/2, Nb = (1 - phi0)/2. With fp16 storage the
+// density reference is rho = 1 and the component references come from the
+// phase grid that k_init_phase wrote (periodic mirrors included).
 template <class S>
 __global__ void __launch_bounds__(kBlock) k_init(DomainView d, const float* phi0, int nx, int ny,
                                                  int px, int pxpy) {
@@ -133,13 +133,11 @@ __global__ void __launch_bounds__(kBlock) k_init(DomainView d, const float* phi0
     if (n >= d.n_sites) return;
     const float p = phi0_of_site(d, n, phi0, nx, ny, px, pxpy);
     const float na = 0.5f * (1.0f + p), nb = 0.5f * (1.0f - p);
-    int nbr[Q7];
+    const int v = d.site_vox[n];
+    unsigned wall = 0;
     if constexpr (S::kRef) {
-        const int v = d.site_vox[n];
-        static_for<1, Q7>([&](auto qc) {
-            constexpr int q = decltype(qc)::value;
-            nbr[q] = __ldg(d.vsite + v + stencil_off(d, q));
-        });
+        d.drho[n] = 0.0f;
+        wall = __ldg(d.wall6 + n);
     }
     const size_t N = d.n_sites;
     static_for<0, Q19>([&](auto qc) {
@@ -148,9 +146,9 @@ __global__ void __launch_bounds__(kBlock) k_init(DomainView d, const float* phi0
         if constexpr (q < Q7) {
             float av = w7(q) * na, bv = w7(q) * nb;
             if constexpr (S::kRef) {
-                const float2 r = d.nab[1][writer_of<q>(n, nbr)];
-                av -= w7(q) * r.x;
-                bv -= w7(q) * r.y;
+                const float pw = writer_phase<0, q>(d, v, wall);
+                av -= w7(q) * 0.5f * (1.0f + pw);
+                bv -= w7(q) * 0.5f * (1.0f - pw);
             }
             S::template st_c<q>(d.a, q * N + n, av);
             S::template st_c<q>(d.b, q * N + n, bv);
@@ -170,12 +168,12 @@ DomainView make_view(const lbpm_ctx* c) {
     d.pxpy = static_cast<int>(c->px * c->py);
     d.site_vox = c->d_site_vox;
     d.vsite = c->d_vsite;
-    d.phi = c->d_phi;
+    d.phi[0] = c->d_phi;
+    d.phi[1] = c->d_phi_alt ? c->d_phi_alt : c->d_phi;
     d.halo_dst = c->d_halo_dst;
     d.halo_site = c->d_halo_site;
+    d.wall6 = c->d_wall6;
     d.nsum = c->d_nsum;
-    d.nab[0] = c->d_nab[0];
-    d.nab[1] = c->d_nab[1];
     d.drho = c->d_drho;
     d.f = c->d_f;
     d.a = c->d_a;
@@ -203,11 +201,16 @@ DomainView make_view(const lbpm_ctx* c) {
 cudaError_t launch_init_fluids(const lbpm_ctx* c, const float* phi0, cudaStream_t s) {
     DomainView d = make_view(c);
     if (c->N == 0) return cudaSuccess;
-    if (c->params.precision == LBPM_FP16) {
-        k_init_ref<<<blocks_for(c->N), kBlock, 0, s>>>(d, phi0, c->nx, c->ny, c->px, c->px * c->py);
+    const bool h = c->params.precision == LBPM_FP16;
+    if (h) {
+        k_init_phase<<<blocks_for(c->N), kBlock, 0, s>>>(d, phi0, c->nx, c->ny, c->px, c->px * c->py);
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess) e = launch_fill_halo(c, s);   // periodic mirrors of the initial phase
+        if (e != cudaSuccess) return e;
         k_init<StoreF16><<<blocks_for(c->N), kBlock, 0, s>>>(d, phi0, c->nx, c->ny, c->px, c->px * c->py);
-    } else
+    } else {
         k_init<StoreF32><<<blocks_for(c->N), kBlock, 0, s>>>(d, phi0, c->nx, c->ny, c->px, c->px * c->py);
+    }
     return cudaGetLastError();
 }
 

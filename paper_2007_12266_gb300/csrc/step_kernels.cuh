@@ -61,22 +61,30 @@ struct StoreF32 {
 };
 
 // fp16 storage of deviations from a local rest-state equilibrium, arithmetic
-// in fp32: f_q - t_q rho(s), A_q - w_q Na(s), B_q - w_q Nb(s), with rho, Na,
-// Nb of a reference site s kept in fp32 per site (DomainView::drho, ::nab).
-// For A, B the reference is the site that wrote the value, at that step. For
-// f it is the writing site for values written at an even step (read at the
-// next odd step through the neighbour table) and the destination site, with
-// its density of the last even step, for values written at an odd step (read
-// at the next even step by that destination with one coalesced load); drho
-// is written only at even steps.
+// in fp32. Momentum: f_q - t_q rho(s), with rho of a reference site s kept in
+// fp32 per site (DomainView::drho): the writing site for values written at an
+// even step (read at the next odd step through the neighbour table) and the
+// destination site, with its density of the last even step, for values
+// written at an odd step (read at the next even step by that destination with
+// one coalesced load); drho is written only at even steps.
+// Components: A_q - w_q (1 + phi_w)/2 and B_q - w_q (1 - phi_w)/2, with phi_w
+// the phase of the site w that wrote the value, at that step. The writer uses
+// its own phase; the reader finds phi_w in the previous step's phase grid
+// (DomainView::phi is double-buffered by step parity) at the upstream voxel
+// x - xi_q, or at its own voxel when that link bounced back (DomainView::wall6),
+// so no neighbour id is looked up for it. Against the writer's own (Na, Nb)
+// the stored number gains w_q (N - 1)(1 +- phi_w)/2; N = Na + Nb follows the
+// density, within a few 1e-2 of 1.
 // Storing A, B themselves let every site of a pure phase round the same value
 // the same way on the fp16 grid, a biased error that leaked 3e-3 of the
 // component mass per 1,000 steps; storing f - t_q left the local density
 // excursion (up to a few 1e-2 under a body force and capillary pressure) in
-// the stored number and cost the velocity its precision. The deviations from
-// the writer's rest state are small, so their rounding is negligible.
+// the stored number and cost the velocity its precision. Referencing the
+// components to the phase of the reading site instead (known to the reader
+// without any lookup) left (phi_w - phi_r)/2, up to w_q at a sharp interface,
+// in the stored numbers and raised the flux error against the oracle tenfold.
 // ld_fdev / st_fdev below exchange the stored number; the kernels add the
-// writer's t_q (rho(s) - 1).
+// reference.
 // Values are scaled by 2^14 (an exact power of two) to keep small deviations
 // out of fp16's subnormal range; |deviation| up to 4 stays representable.
 struct StoreF16 {
@@ -151,11 +159,6 @@ __device__ __forceinline__ size_t read_slot(const DomainView& d, int n, const in
 // ---------------------------------------------------------------------------
 // component populations (D3Q7, Eqs. LBE-mass-a/b)
 // ---------------------------------------------------------------------------
-template <int PAR>
-__device__ __forceinline__ const float2* nab_prev(const DomainView& d) { return d.nab[PAR ^ 1]; }
-template <int PAR>
-__device__ __forceinline__ float2* nab_cur(const DomainView& d) { return d.nab[PAR]; }
-
 // The site that wrote slot read_slot<PAR, Q>(n) during the previous step: the
 // upstream neighbour x - xi_Q if it is a pore, else n itself (bounce-back).
 template <int Q>
@@ -176,26 +179,44 @@ __device__ __forceinline__ int f_ref_read(int n, const int* nb) {
     else return writer_of<Q>(n, nb);
 }
 
-// A_q, B_q of site n at a step of parity PAR (nb[1..6]: face neighbours).
+// Phase of the site that wrote the component value read as direction Q by the
+// site at voxel v at a step of parity PAR (fp16 storage, see StoreF16): from
+// the previous step's phase grid, at the upstream voxel x - xi_Q, or at v when
+// x - xi_Q is solid (bit opp(Q) - 1 of the site's wall mask).
+template <int PAR, int Q>
+__device__ __forceinline__ float writer_phase(const DomainView& d, int v, unsigned wall) {
+    const float* prev = d.phi[PAR ^ 1];
+    if constexpr (Q == 0) {
+        return prev[v];
+    } else {
+        constexpr int o = opp(Q);
+        return prev[((wall >> (o - 1)) & 1u) ? v : v + stencil_off(d, o)];
+    }
+}
+
+// A_q, B_q of site n (voxel v) at a step of parity PAR (nb[1..6]: face
+// neighbours at odd steps).
 template <int PAR, class S>
-__device__ __forceinline__ void load_components(const DomainView& d, int n, const int* nb, float (&a)[Q7],
+__device__ __forceinline__ void load_components(const DomainView& d, int n, int v, const int* nb, float (&a)[Q7],
                                                 float (&b)[Q7]) {
+    unsigned wall = 0;
+    if constexpr (S::kRef) wall = __ldg(d.wall6 + n);
     static_for<0, Q7>([&](auto qc) {
         constexpr int q = decltype(qc)::value;
         const size_t i = read_slot<PAR, q>(d, n, nb);
         a[q] = S::template ld_c<q>(d.a, i);
         b[q] = S::template ld_c<q>(d.b, i);
         if constexpr (S::kRef) {
-            const float2 r = nab_prev<PAR>(d)[writer_of<q>(n, nb)];
-            a[q] = fmaf(w7(q), r.x, a[q]);
-            b[q] = fmaf(w7(q), r.y, b[q]);
+            const float pw = writer_phase<PAR, q>(d, v, wall);
+            a[q] = fmaf(w7(q) * 0.5f, 1.0f + pw, a[q]);
+            b[q] = fmaf(w7(q) * 0.5f, 1.0f - pw, b[q]);
         }
     });
 }
 
 // Whether the face-neighbour ids are needed to read the components.
-template <int PAR, class S>
-constexpr bool need_face_nb() { return PAR == 1 || S::kRef; }
+template <int PAR>
+constexpr bool need_face_nb() { return PAR == 1; }
 
 // ---------------------------------------------------------------------------
 // phase pass: Na, Nb -> phi (dense grid) and N (per site)          Sec. 3.1
@@ -220,7 +241,7 @@ __device__ __forceinline__ void phase_thread(const DomainView& d, int t) {
     int nb[7];
     if (n >= 0) {
         v = __ldg(d.site_vox + n);
-        if constexpr (need_face_nb<PAR, S>()) {
+        if constexpr (need_face_nb<PAR>()) {
             static_for<1, 7>([&](auto qc) {
                 constexpr int q = decltype(qc)::value;
                 nb[q] = __ldg(d.vsite + v + stencil_off(d, q));
@@ -231,7 +252,7 @@ __device__ __forceinline__ void phase_thread(const DomainView& d, int t) {
     allow_next_grid();
     if (n < 0) return;
     float a[Q7], b[Q7];
-    load_components<PAR, S>(d, n, nb, a, b);
+    load_components<PAR, S>(d, n, v, nb, a, b);
     float Na = 0.0f, Nb = 0.0f;
     static_for<0, Q7>([&](auto qc) {
         constexpr int q = decltype(qc)::value;
@@ -241,11 +262,10 @@ __device__ __forceinline__ void phase_thread(const DomainView& d, int t) {
     const float Nt = Na + Nb;
     const float phi = Nt > 0.0f ? (Na - Nb) / Nt : 0.0f;
     if (dst < 0) {
-        d.phi[v] = phi;
-        if constexpr (S::kRef) nab_cur<PAR>(d)[n] = make_float2(Na, Nb);
-        else d.nsum[n] = Nt;
+        d.phi[PAR][v] = phi;
+        d.nsum[n] = Nt;
     } else {
-        d.phi[dst] = phi;    // halo voxel of a periodic face
+        d.phi[PAR][dst] = phi;    // halo voxel of a periodic face
     }
 }
 
@@ -305,20 +325,6 @@ __device__ __forceinline__ void load_f(const DomainView& d, int n, int v, float 
     }
 }
 
-// Na, Nb of site n from the phase pass of this step.
-template <int PAR, class S>
-__device__ __forceinline__ void site_nab(const DomainView& d, int n, float phi_c, float& Na, float& Nb) {
-    if constexpr (S::kRef) {
-        const float2 r = nab_cur<PAR>(d)[n];
-        Na = r.x;
-        Nb = r.y;
-    } else {
-        // Na = N (1 + phi)/2, Nb = N (1 - phi)/2 with N from the phase pass
-        const float Nt = d.nsum[n];
-        Na = 0.5f * Nt * (1.0f + phi_c);
-        Nb = 0.5f * Nt * (1.0f - phi_c);
-    }
-}
 
 // colour gradient C = sum_q g_q xi_q phi(x + xi_q); phi_at(q) gives the
 // neighbour's phase (solids hold phi_s)
@@ -359,10 +365,10 @@ __device__ __forceinline__ Moments moments(const float (&f)[Q19]) {
 // Collision, recoloring and streaming of site n, given its incoming
 // deviations f and their moments, its phase phi_c, Na, Nb and the colour
 // gradient.
+// Nt: Na + Nb from the phase pass (Na = Nt (1 + phi_c)/2, Nb = Nt (1 - phi_c)/2).
 template <int PAR, class S>
 __device__ __forceinline__ void collide_site(const DomainView& d, int n, const float (&f)[Q19], Moments mo,
-                                             float phi_c, float Na, float Nb, float Cx, float Cy, float Cz,
-                                             SlotCache sc) {
+                                             float phi_c, float Nt, float Cx, float Cy, float Cz, SlotCache sc) {
     using T = typename S::T;
     const size_t N = static_cast<size_t>(d.n_sites);
     T* const F = static_cast<T*>(d.f);
@@ -482,12 +488,17 @@ __device__ __forceinline__ void collide_site(const DomainView& d, int n, const f
     // recolored component distributions (Eqs. LBE-mass-a/b), streamed on the
     // fly; the rest populations take the remainder of Na and Nb so that the
     // fp32 weights (whose sum is not exactly 1) create no mass. With fp16
-    // storage the stored quantity is the deviation from w_q Na (w_q Nb), which
-    // the formula gives directly: w_q Na (4.5 u.xi + beta Nb/N n.xi).
+    // storage the stored quantity is the deviation from w_q (1 +- phi_c)/2: the
+    // deviation from w_q Na (w_q Nb), which the formula gives directly as
+    // w_q Na (4.5 u.xi + beta Nb/N n.xi), plus w_q times
+    //   Na - (1 + phi_c)/2 = (N - 1)(1 + phi_c)/2   (likewise for Nb).
     // (working units: Na, Nb times K, j divided by K back to u)
     T* const A = static_cast<T*>(d.a);
     T* const B = static_cast<T*>(d.b);
-    const float NaK = Na * K, NbK = Nb * K;
+    const float NaK = (0.5f * K) * Nt * (1.0f + phi_c), NbK = (0.5f * K) * Nt * (1.0f - phi_c);
+    // fp16 only: K (N - 1)(1 +- phi_c)/2, the offsets of the references
+    const float hN = (0.5f * K) * (Nt - 1.0f);
+    const float eA = hN * (1.0f + phi_c), eB = hN * (1.0f - phi_c);
     float asum = 0.0f, bsum = 0.0f;
     static_for<1, Q7>([&](auto qc) {
         constexpr int q = decltype(qc)::value;
@@ -500,19 +511,28 @@ __device__ __forceinline__ void collide_site(const DomainView& d, int n, const f
             const float du = (4.5f * iK) * ux;
             av = w7(q) * NaK * (du + bxa * nn);
             bv = w7(q) * NbK * (du - bxb * nn);
+            asum += av;
+            bsum += bv;
+            av = fmaf(w7(q), eA, av);
+            bv = fmaf(w7(q), eB, bv);
         } else {
             const float base = fmaf(4.5f * iK, ux, 1.0f);
             av = w7(q) * NaK * (base + bxa * nn);
             bv = w7(q) * NbK * (base - bxb * nn);
+            asum += av;
+            bsum += bv;
         }
-        asum += av;
-        bsum += bv;
         S::st_cs(dst(qc, A), av);
         S::st_cs(dst(qc, B), bv);
     });
     if constexpr (S::kRef) {
-        S::st_cs(A + n, -asum);
-        S::st_cs(B + n, -bsum);
+        // the readers add w_q (1 +- phi_c)/2 to the seven values, which sums to
+        // (1 +- phi_c)/2 times the fp32 weights' sum 1 + 2^-26; the rest value
+        // takes Na (1 - that sum) so that the values still add up to Na
+        constexpr double kWsum = static_cast<double>(w7(0)) + 6.0 * static_cast<double>(w7(1));
+        constexpr float kWerr = static_cast<float>(1.0 - kWsum);
+        S::st_cs(A + n, fmaf(kWerr, NaK, fmaf(w7(0), eA, -asum)));
+        S::st_cs(B + n, fmaf(kWerr, NbK, fmaf(w7(0), eB, -bsum)));
     } else {
         S::st_cs(A + n, NaK - asum);
         S::st_cs(B + n, NbK - bsum);
@@ -532,12 +552,12 @@ __device__ __forceinline__ void collide_thread(const DomainView& d, int n, SlotC
     allow_next_grid();
     wait_prior_grid();
 
-    const float* pv = d.phi + v;
+    const float* pv = d.phi[PAR] + v;
     const float phi_c = *pv;
-    float Na, Nb, Cx, Cy, Cz;
-    site_nab<PAR, S>(d, n, phi_c, Na, Nb);
+    const float Nt = d.nsum[n];
+    float Cx, Cy, Cz;
     color_gradient([&](auto qc) { return pv[stencil_off(d, decltype(qc)::value)]; }, Cx, Cy, Cz);
-    collide_site<PAR, S>(d, n, f, moments(f), phi_c, Na, Nb, Cx, Cy, Cz, sc);
+    collide_site<PAR, S>(d, n, f, moments(f), phi_c, Nt, Cx, Cy, Cz, sc);
 }
 
 // ---------------------------------------------------------------------------
@@ -549,12 +569,14 @@ __device__ __forceinline__ void reservoir_thread(const DomainView& d, int n, int
                                                  float rho_out) {
     const int v = d.site_vox[n];
     int nb[Q19];
-    if constexpr (PAR == 1 || S::kRef) {
+    if constexpr (PAR == 1) {
         static_for<1, Q19>([&](auto qc) {
             constexpr int q = decltype(qc)::value;
             nb[q] = __ldg(d.vsite + v + stencil_off(d, q));
         });
     }
+    // fp16: the component references of the next step's reads (see StoreF16)
+    const unsigned wall = S::kRef ? __ldg(d.wall6 + n) : 0u;
     const float rho = side == 1 ? rho_in : rho_out;
     const float na = side == 1 ? 1.0f : 0.0f;
     static_for<0, Q19>([&](auto qc) {
@@ -569,10 +591,9 @@ __device__ __forceinline__ void reservoir_thread(const DomainView& d, int n, int
         if constexpr (q < Q7) {
             float av = w7(q) * na, bv = w7(q) * (1.0f - na);
             if constexpr (S::kRef) {
-                // the next step reconstructs with the writer's densities of this step
-                const float2 r = nab_prev<PAR>(d)[writer_of<q>(n, nb)];
-                av -= w7(q) * r.x;
-                bv -= w7(q) * r.y;
+                const float pw = writer_phase<PAR, q>(d, v, wall);
+                av -= w7(q) * 0.5f * (1.0f + pw);
+                bv -= w7(q) * 0.5f * (1.0f - pw);
             }
             S::template st_c<q>(d.a, i, av);
             S::template st_c<q>(d.b, i, bv);
@@ -603,7 +624,7 @@ template <int PAR, class S>
 __device__ __forceinline__ float face_deviations(const DomainView& d, int n, float sgn, int (&nb)[Q19],
                                                  float (&dv)[Q19], float& nx, float& ny) {
     const int v = d.site_vox[n];
-    if constexpr (PAR == 1 || S::kRef) {
+    if constexpr (PAR == 1) {
         static_for<1, Q19>([&](auto qc) {
             constexpr int q = decltype(qc)::value;
             nb[q] = __ldg(d.vsite + v + stencil_off(d, q));
@@ -672,9 +693,10 @@ __device__ __forceinline__ void pressure_face_thread(const DomainView& d, int n,
             const float eq = w7(q) * rho * (1.0f + 4.5f * cz(q) * uz);
             float av = side == 1 ? eq : 0.0f, bv = side == 1 ? 0.0f : eq;
             if constexpr (S::kRef) {
-                const float2 r = nab_prev<PAR>(d)[writer_of<q>(n, nb)];
-                av -= w7(q) * r.x;
-                bv -= w7(q) * r.y;
+                // the reference the next step reads it with (see StoreF16)
+                const float pw = writer_phase<PAR, q>(d, d.site_vox[n], __ldg(d.wall6 + n));
+                av -= w7(q) * 0.5f * (1.0f + pw);
+                bv -= w7(q) * 0.5f * (1.0f - pw);
             }
             const size_t i = read_slot<PAR, q>(d, n, nb);
             S::template st_c<q>(d.a, i, av);
