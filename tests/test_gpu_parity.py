@@ -337,6 +337,28 @@ def test_full_size_steady256_two_steps():
         assert max(ef, ea, eb) <= 1e-6, (ef, ea, eb)
 
 
+def test_full_size_steady256_fp16_two_steps():
+    """The bench workload with fp16 storage: after init and after each of one
+    even and one odd step, the oracle restarts from what the fp16 store holds
+    and one step of both must agree within the storage tolerance of the 32^3
+    fp16 test, at every site."""
+    from synthetic import workload_steady256
+    w = workload_steady256()
+    dom, ref = pair(w.labels, w.affinity, w.periodic, tau_a=w.tau_a, tau_b=w.tau_b,
+                    alpha=w.alpha, beta=w.beta, force=w.force, precision="fp16")
+    dom.init_fluids(w.phi0)
+    for step in (0, 1):
+        held = [dom.distributions(k).astype(np.float64) for k in ("f", "a", "b")]
+        ref.set_state(*held, step=step)
+        dom.advance(1)
+        ref.step(1)
+        f, A, B = ref.state()
+        ef = np.abs(dom.distributions("f") - f) / T19[:, None]
+        assert ef.max() < 5e-5, (step, ef.max())
+        assert rel_err(dom.distributions("a"), A, W7).max() < 2e-3, step
+        assert rel_err(dom.distributions("b"), B, W7).max() < 2e-3, step
+
+
 def test_graph_bundles_match_plain_launches():
     """advance() replays captured step bundles; with kernel timing on it
     launches every kernel on its own. Both orders of work are the same, so the
