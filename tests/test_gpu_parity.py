@@ -340,8 +340,12 @@ def test_full_size_steady256_two_steps():
 def test_full_size_steady256_fp16_two_steps():
     """The bench workload with fp16 storage: after init and after each of one
     even and one odd step, the oracle restarts from what the fp16 store holds
-    and one step of both must agree within the storage tolerance of the 32^3
-    fp16 test, at every site."""
+    and one step of both must agree at every site within the storage
+    precision. fp16 rounds a stored deviation to 2^-11 of itself; the first
+    steps from the sharp blob interfaces leave deviations f_q - t_q rho of up
+    to 0.17 t_q, so f is held to 2^-10 times the largest deviation of the
+    step's result (twice the half-ulp, for the rounding of the inputs carried
+    through one collision); A and B to the 2e-3 (floor w_q) of the 32^3 test."""
     from synthetic import workload_steady256
     w = workload_steady256()
     dom, ref = pair(w.labels, w.affinity, w.periodic, tau_a=w.tau_a, tau_b=w.tau_b,
@@ -353,8 +357,9 @@ def test_full_size_steady256_fp16_two_steps():
         dom.advance(1)
         ref.step(1)
         f, A, B = ref.state()
+        dev = (np.abs(f - T19[:, None] * f.sum(axis=0)) / T19[:, None]).max()
         ef = np.abs(dom.distributions("f") - f) / T19[:, None]
-        assert ef.max() < 5e-5, (step, ef.max())
+        assert ef.max() < 2.0 ** -10 * dev, (step, ef.max(), dev)
         assert rel_err(dom.distributions("a"), A, W7).max() < 2e-3, step
         assert rel_err(dom.distributions("b"), B, W7).max() < 2e-3, step
 
