@@ -244,6 +244,16 @@ lbpm_status lbpm_read_field_noalloc(lbpm_ctx* ctx, int which, float* out_dense);
  * will collide, whatever the AA parity. Q = 19 for F, 7 for A, B. */
 lbpm_status lbpm_read_distributions(lbpm_ctx* ctx, int which, float* out_canonical);
 
+/* Distributions of the current state at the voxels of a sub-box of the image
+ * (a library service for probing a large domain without exporting it whole):
+ * lo[3], hi[3] are voxel bounds (x, y, z) with 0 <= lo < hi <= (nx, ny, nz);
+ * out (caller-allocated, Q*bx*by*bz floats, b = hi - lo) receives
+ * out[q*bx*by*bz + (z*by + y)*bx + x] = f_q (A_q, B_q) of the voxel lo + (x, y, z)
+ * in canonical order as lbpm_read_distributions gives it, NaN at solid voxels.
+ * Errors: LBPM_E_INVALID (NULL pointer, unknown set, box empty or outside the
+ * image), LBPM_E_STATE (no fluids), LBPM_E_OOM, LBPM_E_CUDA. */
+lbpm_status lbpm_read_box(lbpm_ctx* ctx, int which, const int* lo, const int* hi, float* out);
+
 /* Overwrite one distribution set from canonical order (same layout as
  * lbpm_read_distributions) at the current step parity. */
 lbpm_status lbpm_write_distributions(lbpm_ctx* ctx, int which, const float* in_canonical);

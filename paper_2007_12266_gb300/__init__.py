@@ -308,6 +308,20 @@ class Domain:
         self._check(self._L.lbpm_read_distributions(self._h, code, out.ctypes.data))
         return out
 
+    def read_box(self, which: str, lo, hi) -> np.ndarray:
+        """Distributions (canonical order) at the voxels of the box [lo, hi)
+        given as (x, y, z) bounds: array [Q][bz][by][bx], NaN at solids."""
+        code, Q = DISTS[which]
+        l = np.ascontiguousarray(lo, dtype=np.int32)
+        h = np.ascontiguousarray(hi, dtype=np.int32)
+        if l.shape != (3,) or h.shape != (3,):
+            raise ValueError("lo and hi take three voxel bounds (x, y, z)")
+        ext = h - l
+        out = np.empty((Q, int(ext[2]), int(ext[1]), int(ext[0])) if (ext > 0).all() else (Q, 0, 0, 0),
+                       dtype=np.float32)
+        self._check(self._L.lbpm_read_box(self._h, code, l.ctypes.data, h.ctypes.data, out.ctypes.data))
+        return out
+
     def write_distributions(self, which: str, values: np.ndarray):
         code, Q = DISTS[which]
         v = np.ascontiguousarray(values, dtype=np.float32)

@@ -94,6 +94,7 @@ SIGNATURES = {
     "lbpm_read_field": (ct.c_int, [c_ctx_p, ct.c_int, ct.c_void_p]),
     "lbpm_read_field_noalloc": (ct.c_int, [c_ctx_p, ct.c_int, ct.c_void_p]),
     "lbpm_read_distributions": (ct.c_int, [c_ctx_p, ct.c_int, ct.c_void_p]),
+    "lbpm_read_box": (ct.c_int, [c_ctx_p, ct.c_int, ct.c_void_p, ct.c_void_p, ct.c_void_p]),
     "lbpm_write_distributions": (ct.c_int, [c_ctx_p, ct.c_int, ct.c_void_p]),
     "lbpm_num_sites": (ct.c_int, [c_ctx_p, ct.POINTER(ct.c_longlong)]),
     "lbpm_step_count": (ct.c_int, [c_ctx_p, ct.POINTER(ct.c_longlong)]),

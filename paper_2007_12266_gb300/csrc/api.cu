@@ -668,6 +668,30 @@ lbpm_status lbpm_read_distributions(lbpm_ctx* c, int which, float* out) {
     return LBPM_OK;
 }
 
+lbpm_status lbpm_read_box(lbpm_ctx* c, int which, const int* lo, const int* hi, float* out) {
+    lbpm_status s = enter(c);
+    if (s) return s;
+    if (!lo || !hi || !out) return fail(c, LBPM_E_INVALID, "lo, hi and out must not be NULL");
+    if (which < LBPM_DIST_F || which > LBPM_DIST_B) return fail(c, LBPM_E_INVALID, "unknown distribution");
+    if (!c->have_fluids) return fail(c, LBPM_E_STATE, "initialise the fluids first");
+    const int dims[3] = {c->nx, c->ny, c->nz};
+    long long nbox = 1;
+    for (int a = 0; a < 3; ++a) {
+        if (lo[a] < 0 || hi[a] > dims[a] || lo[a] >= hi[a]) return fail(c, LBPM_E_INVALID, "box outside the image or empty");
+        nbox *= hi[a] - lo[a];
+    }
+    const long long count = (which == LBPM_DIST_F ? 19 : 7) * nbox;
+    float* d;
+    LBPM_ALLOC(c, d, float, count);
+    cudaError_t e = launch_read_box(c, static_cast<int>(c->step & 1), which, lo, hi, d, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, d, sizeof(float) * count, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    dfree(c, d);
+    if (e != cudaSuccess) return fail_cuda(c, "read_box", e);
+    c->launches += 1;
+    return LBPM_OK;
+}
+
 lbpm_status lbpm_write_distributions(lbpm_ctx* c, int which, const float* in) {
     lbpm_status s = enter(c);
     if (s) return s;

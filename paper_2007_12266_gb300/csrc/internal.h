@@ -169,6 +169,8 @@ int batch_max_blocks(int kernel, bool fp16, int bt);
 cudaError_t launch_measure(lbpm_ctx* c, int parity, double* d_out, cudaStream_t s);
 cudaError_t launch_field(const lbpm_ctx* c, int parity, int which, float* dense, cudaStream_t s);
 cudaError_t launch_export_dist(const lbpm_ctx* c, int parity, int which, float* out, cudaStream_t s);
+cudaError_t launch_read_box(const lbpm_ctx* c, int parity, int which, const int* lo, const int* hi, float* out,
+                            cudaStream_t s);
 cudaError_t launch_import_dist(const lbpm_ctx* c, int parity, int which, const float* in, cudaStream_t s);
 
 }  // namespace lbm

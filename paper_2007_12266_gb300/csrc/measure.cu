@@ -96,6 +96,28 @@ __global__ void __launch_bounds__(kBlock) k_export(DomainView d, int which, floa
     }
 }
 
+// Canonical distributions of the voxels of a sub-box [lo, hi) of the image,
+// one thread per box voxel, out[q][box voxel] (x fastest); solids NaN.
+template <int PAR, class S>
+__global__ void __launch_bounds__(kBlock) k_box(DomainView d, int which, int3 lo, int3 ext, float* out) {
+    const long long nbox = static_cast<long long>(ext.x) * ext.y * ext.z;
+    const long long i = static_cast<long long>(blockIdx.x) * kBlock + threadIdx.x;
+    if (i >= nbox) return;
+    const int x = static_cast<int>(i % ext.x), r = static_cast<int>(i / ext.x);
+    const int y = r % ext.y, z = r / ext.y;
+    const int pv = (lo.x + x + 1) + d.px * (lo.y + y + 1) + d.pxpy * (lo.z + z + 1);
+    const int n = d.vsite[pv];
+    const int Q = which == LBPM_DIST_F ? Q19 : Q7;
+    if (n < 0) {
+        for (int q = 0; q < Q; ++q) out[q * nbox + i] = __int_as_float(0x7fc00000);   // NaN
+        return;
+    }
+    float f[Q19], a[Q7], b[Q7];
+    load_site<PAR, S>(d, n, f, a, b);
+    const float* v = which == LBPM_DIST_F ? f : (which == LBPM_DIST_A ? a : b);
+    for (int q = 0; q < Q; ++q) out[q * nbox + i] = v[q];
+}
+
 // fp16 store: the reference density of imported momentum populations is the
 // sum of the imported values at each site (any reference works as long as the
 // reader uses the same one); imported component values are stored relative to
@@ -181,6 +203,12 @@ struct ExportK {
     }
 };
 template <int PAR, class S>
+struct BoxK {
+    static void launch(unsigned g, cudaStream_t s, DomainView d, int w, int3 lo, int3 ext, float* o) {
+        k_box<PAR, S><<<g, kBlock, 0, s>>>(d, w, lo, ext, o);
+    }
+};
+template <int PAR, class S>
 struct ImportK {
     static void launch(unsigned g, cudaStream_t s, DomainView d, int w, const float* i) {
         k_import<PAR, S><<<g, kBlock, 0, s>>>(d, w, i);
@@ -216,6 +244,14 @@ cudaError_t launch_field(const lbpm_ctx* c, int parity, int which, float* dense,
 
 cudaError_t launch_export_dist(const lbpm_ctx* c, int parity, int which, float* out, cudaStream_t s) {
     return dispatch<ExportK>(c, parity, blocks_for(c->N), s, make_view(c), which, out);
+}
+
+cudaError_t launch_read_box(const lbpm_ctx* c, int parity, int which, const int* lo, const int* hi, float* out,
+                            cudaStream_t s) {
+    const int3 l = make_int3(lo[0], lo[1], lo[2]);
+    const int3 ext = make_int3(hi[0] - lo[0], hi[1] - lo[1], hi[2] - lo[2]);
+    const long long nbox = static_cast<long long>(ext.x) * ext.y * ext.z;
+    return dispatch<BoxK>(c, parity, blocks_for(nbox), s, make_view(c), which, l, ext, out);
 }
 
 cudaError_t launch_import_dist(const lbpm_ctx* c, int parity, int which, const float* in, cudaStream_t s) {
