@@ -66,8 +66,10 @@ void free_state(lbpm_ctx* c) {
     dfree(c, c->d_nsum);
     dfree(c, c->d_drho);
     dfree(c, c->d_phi_alt);
+    dfree(c, c->d_rsum);
     c->d_drho = nullptr;
     c->d_phi_alt = nullptr;
+    c->d_rsum = nullptr;
     c->d_f = c->d_a = c->d_b = nullptr;
     c->d_nsum = nullptr;
     c->have_fluids = false;
@@ -113,8 +115,9 @@ lbpm_status alloc_state(lbpm_ctx* c) {
         // the second phase grid starts as a copy of the first (solids, walls
         // and their periodic mirrors are static and the same in both)
         c->d_drho = static_cast<float*>(dalloc(c, sizeof(float) * c->N));
+        c->d_rsum = static_cast<float*>(dalloc(c, sizeof(float) * c->N));
         c->d_phi_alt = static_cast<float*>(dalloc(c, sizeof(float) * c->Vp));
-        ok = ok && c->d_drho && c->d_phi_alt;
+        ok = ok && c->d_drho && c->d_rsum && c->d_phi_alt;
         if (ok && cudaMemcpyAsync(c->d_phi_alt, c->d_phi, sizeof(float) * c->Vp, cudaMemcpyDeviceToDevice,
                                   c->stream) != cudaSuccess)
             ok = false;
@@ -546,7 +549,7 @@ lbpm_status lbpm_init_fluids(lbpm_ctx* c, const float* phi0) {
     c->step = 0;
     c->have_fluids = true;
     c->unstable = false;
-    c->launches += c->params.precision == LBPM_FP16 ? 4 : 2;
+    c->launches += c->params.precision == LBPM_FP16 ? 5 : 2;
     return LBPM_OK;
 }
 

@@ -32,6 +32,8 @@ struct DomainView {
     const int* halo_site;  // [H] site it mirrors
     const unsigned char* wall6;  // [N] bit q - 1 set when x + xi_q (q = 1..6) is solid or wall
     float* nsum;           // [N] Na + Nb of the current step (phase pass -> collision)
+    float* rsum;           // [N] fp16 store: sum_q w_q phi_w(q) of the component references that the
+                           //     next phase pass reads (collision -> phase pass, see StoreF16)
     float* drho;           // [N] rho - 1 of each site at the last even step, fp16 store: the
                            //     reference of the stored momentum deviations
     void* f;               // [19][N] momentum distributions (AA in place)
@@ -81,6 +83,7 @@ struct lbpm_ctx {
     int* d_halo_site = nullptr;     // [H]
     unsigned char* d_wall6 = nullptr;  // [N] face links that bounce back
     float* d_nsum = nullptr;        // [N]
+    float* d_rsum = nullptr;        // [N] fp16 storage
     double* d_face_part = nullptr;          // flux inlet: per-block sums (2 * kFaceBlocks)
     float* d_face_rho = nullptr;            // flux inlet: (rho, rho - 1) of the inlet face
     float* d_drho = nullptr;                // [N] fp16 store
@@ -130,6 +133,7 @@ cudaError_t launch_wall_mask(const lbpm_ctx* c, cudaStream_t s);
 
 DomainView make_view(const lbpm_ctx* c);
 cudaError_t launch_init_fluids(const lbpm_ctx* c, const float* phi0, cudaStream_t s);
+cudaError_t launch_ref_sum(const lbpm_ctx* c, int parity, cudaStream_t s);
 cudaError_t launch_phase(const lbpm_ctx* c, int parity, cudaStream_t s);
 cudaError_t launch_collide(const lbpm_ctx* c, int parity, cudaStream_t s);
 cudaError_t launch_reservoir(const lbpm_ctx* c, int parity, cudaStream_t s);

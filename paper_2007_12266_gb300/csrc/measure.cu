@@ -260,7 +260,9 @@ cudaError_t launch_import_dist(const lbpm_ctx* c, int parity, int which, const f
         const cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
-    return dispatch<ImportK>(c, parity, blocks_for(c->N), s, make_view(c), which, in);
+    const cudaError_t e = dispatch<ImportK>(c, parity, blocks_for(c->N), s, make_view(c), which, in);
+    if (e != cudaSuccess) return e;
+    return launch_ref_sum(c, parity, s);   // fp16: the phase pass's references of the imported state
 }
 
 }  // namespace lbm

@@ -99,8 +99,8 @@ size_t estimate_footprint(const lbpm_job_spec& sp, long long n_pore) {
     const double N = static_cast<double>(n_pore);
     const double es = sp.params.precision == LBPM_FP16 ? 2.0 : 4.0;
     const bool h = sp.params.precision == LBPM_FP16;
-    // populations, nsum (+ drho and the second phase grid with fp16 storage)
-    const double state = 33.0 * es * N + (h ? 8.0 : 4.0) * N + (h ? 4.0 * Vp : 0.0);
+    // populations, nsum (+ drho, rsum and the second phase grid with fp16 storage)
+    const double state = 33.0 * es * N + (h ? 12.0 : 4.0) * N + (h ? 4.0 * Vp : 0.0);
     // labels, vsite, phi, site_vox, wall mask
     const double grids = 2.0 * V + 8.0 * Vp + 5.0 * N;
     const double transient = 8.0 * Vp;

@@ -122,6 +122,15 @@ __global__ void __launch_bounds__(kBlock) k_init_phase(DomainView d, const float
     d.phi[1][d.site_vox[n]] = phi0_of_site(d, n, phi0, nx, ny, px, pxpy);
 }
 
+// fp16 storage: the references' phase sum of every site for a step of parity
+// PAR (what the collision stores in rsum), after an initialisation or an import.
+template <int PAR>
+__global__ void __launch_bounds__(kBlock) k_ref_sum(DomainView d) {
+    const int n = blockIdx.x * kBlock + threadIdx.x;
+    if (n >= d.n_sites) return;
+    d.rsum[n] = reference_phase_sum<PAR>(d, n, d.site_vox[n]);
+}
+
 // Initial state consistent with phi0 (rho = 1, u = 0), written in the even
 // (natural) layout: Na = (1 + phi0)/2, Nb = (1 - phi0)/2. With fp16 storage the
 // density reference is rho = 1 and the component references come from the
@@ -175,6 +184,7 @@ DomainView make_view(const lbpm_ctx* c) {
     d.wall6 = c->d_wall6;
     d.nsum = c->d_nsum;
     d.drho = c->d_drho;
+    d.rsum = c->d_rsum;
     d.f = c->d_f;
     d.a = c->d_a;
     d.b = c->d_b;
@@ -208,9 +218,17 @@ cudaError_t launch_init_fluids(const lbpm_ctx* c, const float* phi0, cudaStream_
         if (e == cudaSuccess) e = launch_fill_halo(c, s);   // periodic mirrors of the initial phase
         if (e != cudaSuccess) return e;
         k_init<StoreF16><<<blocks_for(c->N), kBlock, 0, s>>>(d, phi0, c->nx, c->ny, c->px, c->px * c->py);
+        k_ref_sum<0><<<blocks_for(c->N), kBlock, 0, s>>>(d);
     } else {
         k_init<StoreF32><<<blocks_for(c->N), kBlock, 0, s>>>(d, phi0, c->nx, c->ny, c->px, c->px * c->py);
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ref_sum(const lbpm_ctx* c, int parity, cudaStream_t s) {
+    if (c->params.precision != LBPM_FP16 || c->N == 0) return cudaSuccess;
+    if (parity == 0) k_ref_sum<0><<<blocks_for(c->N), kBlock, 0, s>>>(make_view(c));
+    else k_ref_sum<1><<<blocks_for(c->N), kBlock, 0, s>>>(make_view(c));
     return cudaGetLastError();
 }
 

@@ -72,7 +72,12 @@ struct StoreF32 {
 // its own phase; the reader finds phi_w in the previous step's phase grid
 // (DomainView::phi is double-buffered by step parity) at the upstream voxel
 // x - xi_q, or at its own voxel when that link bounced back (DomainView::wall6),
-// so no neighbour id is looked up for it. Against the writer's own (Na, Nb)
+// so no neighbour id is looked up for it. The phase pass needs only the sum
+// of the references over the seven directions, Na = sum_q s_q + (sum_q w_q +
+// S)/2 with S = sum_q w_q phi_w(q) (likewise Nb with -S); the collision, which
+// holds those phases for its colour gradient, stores S per site
+// (DomainView::rsum), so the phase pass reads one coalesced number instead of
+// six phases. Against the writer's own (Na, Nb)
 // the stored number gains w_q (N - 1)(1 +- phi_w)/2; N = Na + Nb follows the
 // density, within a few 1e-2 of 1.
 // Storing A, B themselves let every site of a pure phase round the same value
@@ -214,6 +219,19 @@ __device__ __forceinline__ void load_components(const DomainView& d, int n, int 
     });
 }
 
+// fp16 storage: S = sum_q w_q phi_w(q) over the seven component values that
+// site n (voxel v) reads at a step of parity PAR (see writer_phase).
+template <int PAR>
+__device__ __forceinline__ float reference_phase_sum(const DomainView& d, int n, int v) {
+    const unsigned wall = __ldg(d.wall6 + n);
+    float S = 0.0f;
+    static_for<0, Q7>([&](auto qc) {
+        constexpr int q = decltype(qc)::value;
+        S = fmaf(w7(q), writer_phase<PAR, q>(d, v, wall), S);
+    });
+    return S;
+}
+
 // Whether the face-neighbour ids are needed to read the components.
 template <int PAR>
 constexpr bool need_face_nb() { return PAR == 1; }
@@ -251,14 +269,28 @@ __device__ __forceinline__ void phase_thread(const DomainView& d, int t) {
     wait_prior_grid();
     allow_next_grid();
     if (n < 0) return;
-    float a[Q7], b[Q7];
-    load_components<PAR, S>(d, n, v, nb, a, b);
     float Na = 0.0f, Nb = 0.0f;
-    static_for<0, Q7>([&](auto qc) {
-        constexpr int q = decltype(qc)::value;
-        Na += a[q];
-        Nb += b[q];
-    });
+    if constexpr (S::kRef) {
+        // stored deviations plus the references' sum, (1 +- rsum)/2 (the
+        // writers' rest values absorb the fp32 weights' excess over 1)
+        static_for<0, Q7>([&](auto qc) {
+            constexpr int q = decltype(qc)::value;
+            const size_t i = read_slot<PAR, q>(d, n, nb);
+            Na += S::template ld_c<q>(d.a, i);
+            Nb += S::template ld_c<q>(d.b, i);
+        });
+        const float Sr = d.rsum[n];
+        Na = fmaf(0.5f, 1.0f + Sr, Na);
+        Nb = fmaf(0.5f, 1.0f - Sr, Nb);
+    } else {
+        float a[Q7], b[Q7];
+        load_components<PAR, S>(d, n, v, nb, a, b);
+        static_for<0, Q7>([&](auto qc) {
+            constexpr int q = decltype(qc)::value;
+            Na += a[q];
+            Nb += b[q];
+        });
+    }
     const float Nt = Na + Nb;
     const float phi = Nt > 0.0f ? (Na - Nb) / Nt : 0.0f;
     if (dst < 0) {
@@ -526,13 +558,16 @@ __device__ __forceinline__ void collide_site(const DomainView& d, int n, const f
         S::st_cs(dst(qc, B), bv);
     });
     if constexpr (S::kRef) {
-        // the readers add w_q (1 +- phi_c)/2 to the seven values, which sums to
-        // (1 +- phi_c)/2 times the fp32 weights' sum 1 + 2^-26; the rest value
-        // takes Na (1 - that sum) so that the values still add up to Na
+        // The phase pass adds (1 + S)/2 to the seven values a site reads, S
+        // holding w_q phi_c for this site's value of direction q; the seven
+        // stored values above sum to Wsum (Na - (1 + phi_c)/2) with Wsum the
+        // fp32 weights' sum 1 + 2^-26. The rest value takes the difference,
+        // K (1 - Wsum)(Na - 1/2), so that its readers rebuild exactly Na (and
+        // Nb) and the fp32 weights create no mass.
         constexpr double kWsum = static_cast<double>(w7(0)) + 6.0 * static_cast<double>(w7(1));
         constexpr float kWerr = static_cast<float>(1.0 - kWsum);
-        S::st_cs(A + n, fmaf(kWerr, NaK, fmaf(w7(0), eA, -asum)));
-        S::st_cs(B + n, fmaf(kWerr, NbK, fmaf(w7(0), eB, -bsum)));
+        S::st_cs(A + n, fmaf(kWerr, fmaf(-0.5f, K, NaK), fmaf(w7(0), eA, -asum)));
+        S::st_cs(B + n, fmaf(kWerr, fmaf(-0.5f, K, NbK), fmaf(w7(0), eB, -bsum)));
     } else {
         S::st_cs(A + n, NaK - asum);
         S::st_cs(B + n, NbK - bsum);
@@ -557,6 +592,18 @@ __device__ __forceinline__ void collide_thread(const DomainView& d, int n, SlotC
     const float Nt = d.nsum[n];
     float Cx, Cy, Cz;
     color_gradient([&](auto qc) { return pv[stencil_off(d, decltype(qc)::value)]; }, Cx, Cy, Cz);
+    if constexpr (S::kRef) {
+        // references of the values the next phase pass reads at this site: the
+        // phase of x - xi_q, which this step writes, or this site's own on a
+        // bounce-back link; every face direction has the same weight
+        const unsigned wall = __ldg(d.wall6 + n);
+        float Sf = 0.0f;
+        static_for<1, Q7>([&](auto qc) {
+            constexpr int q = decltype(qc)::value;
+            Sf += (wall >> (q - 1)) & 1u ? phi_c : pv[stencil_off(d, q)];
+        });
+        d.rsum[n] = fmaf(w7(1), Sf, w7(0) * phi_c);
+    }
     collide_site<PAR, S>(d, n, f, moments(f), phi_c, Nt, Cx, Cy, Cz, sc);
 }
 
