@@ -184,21 +184,38 @@ def test_mass_conservation_fp32():
         assert abs(m1[k] / m0[k] - 1) < 2e-6, k
 
 
-def test_reservoir_slabs_parity():
+@pytest.mark.parametrize("precision", ["fp32", "fp16"])
+def test_reservoir_slabs_parity(precision):
     sp = sphere_pack((12, 10, 24), 0.55, 2.0, 0.5, 17)
     lab = sp.labels
     aff = uniform_affinity(lab, -0.7)
     kw = dict(KW, reservoir_z=1, rho_in=1.001, rho_out=0.999)
     per = (1, 1, 0)
-    dom, ref = pair(lab, aff, per, **kw)
+    dom, ref = pair(lab, aff, per, precision=precision, **kw)
     phi0 = np.full(lab.shape, -1.0, np.float32)
     dom.init_fluids(phi0)
     ref.init_fluids(phi0)
-    assert max(compare_state(dom, ref)) < 1e-7
-    for _ in range(3):
-        dom.advance(1)
-        ref.step(1)
-        assert max(compare_state(dom, ref)) <= 1e-6
+    if precision == "fp32":
+        assert max(compare_state(dom, ref)) < 1e-7
+        for _ in range(3):
+            dom.advance(1)
+            ref.step(1)
+            assert max(compare_state(dom, ref)) <= 1e-6
+    else:
+        # one step from what the fp16 store holds, at both parities, within
+        # the storage bounds of the fp16 one-step test (the slab reset writes
+        # its rest state through the same component references)
+        ef, ea, eb = compare_state(dom, ref)
+        assert ef < 5e-5 and max(ea, eb) < 2e-3
+        for step in range(3):
+            held = [dom.distributions(k).astype(np.float64) for k in ("f", "a", "b")]
+            ref.set_state(*held, step=step)
+            dom.advance(1)
+            ref.step(1)
+            f, A, B = ref.state()
+            assert (np.abs(dom.distributions("f") - f) / T19[:, None]).max() < 5e-5, step
+            assert rel_err(dom.distributions("a"), A, W7).max() < 2e-3, step
+            assert rel_err(dom.distributions("b"), B, W7).max() < 2e-3, step
     dom.advance(197)
     ref.step(197)
     m, mo = dom.measure(), ref.measure()
