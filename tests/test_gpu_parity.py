@@ -334,6 +334,43 @@ def test_edge_cases():
         dom.restore(b"\0" * 40)                      # corrupt snapshot
 
 
+DEGENERATE = [
+    ("thin_periodic_column", (11, 1, 1), (1, 1, 1)),   # x and y neighbours wrap onto the site itself
+    ("two_voxel_slab", (9, 1, 2), (1, 1, 0)),          # z walls, x of width 2, y of width 1
+    ("single_pore", (3, 3, 3), (0, 0, 0)),             # every link bounces back
+]
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp16"])
+@pytest.mark.parametrize("name,shape,periodic", DEGENERATE, ids=[c[0] for c in DEGENERATE])
+def test_degenerate_domains_one_step(name, shape, periodic, precision):
+    """One even and one odd step on domains whose neighbours are the site
+    itself or solid on most links, from the same state on both sides: FP32
+    within 1e-6 max(|o|, w_q); FP16 from the state its store holds, within
+    the bounds of the fp16 one-step test."""
+    lab = np.zeros(shape, np.uint16)
+    if name == "single_pore":
+        lab[:] = 1
+        lab[1, 1, 1] = 0
+    aff = uniform_affinity(lab, 0.3)
+    dom, ref = pair(lab, aff, periodic, precision=precision, **KW)
+    for step in (0, 1):
+        st = random_state(ref, seed=11 + step, amp=0.02)
+        set_both(dom, ref, st, step)
+        if precision == "fp16":
+            held = [dom.distributions(k).astype(np.float64) for k in ("f", "a", "b")]
+            ref.set_state(*held, step=step)
+        dom.advance(1)
+        ref.step(1)
+        if precision == "fp32":
+            assert max(compare_state(dom, ref)) <= 1e-6, step
+        else:
+            f, A, B = ref.state()
+            assert (np.abs(dom.distributions("f") - f) / T19[:, None]).max() < 5e-5, step
+            assert rel_err(dom.distributions("a"), A, W7).max() < 2e-3, step
+            assert rel_err(dom.distributions("b"), B, W7).max() < 2e-3, step
+
+
 def test_full_size_steady256_two_steps():
     """The bench workload (256^3 pack, 3.6 M sites) at full size: bit-exact
     index, then one even and one odd step against the oracle at every site."""
