@@ -36,6 +36,17 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+# the headline metric: pore-site MLUPS of the 256^3 steady-state workload in FP32
+# storage, with the HBM fraction, the FP16-storage run and the batched-job
+# latencies reported beside it in the same line
+METRIC = "pore-site MLUPS + % HBM peak, FP16-store vs FP32; p50/p99 batched-job latency"
+
+
+def workload_label(w, size: int) -> str:
+    return (f"{w.name}: {size}^3 sphere pack, porosity {w.porosity:.3f}, z periodic, x/y walls, "
+            f"Sw=0.4 blobs")
+
+
 # algorithmic bytes per pore site and timestep (FP32 storage)
 BYTES_COLLIDE_FP32 = 19 * 4 * 2 + 14 * 4 + 4      # f read+write, A/B write, own phi read = 212
 BYTES_PHASE_FP32 = 14 * 4 + 4                     # A/B read, phi write = 60
@@ -205,11 +216,12 @@ def bench_reference(args):
     total = sum(timed)
     value = n * len(timed) / total / 1e6
     line = {
-        "impl": "reference", "metric": "pore-site MLUPS", "value": value, "unit": "MLUPS",
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "MLUPS",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * total / len(timed), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": w.name, "n_sites": n, "timesteps_per_step": 1,
+        "config": {"workload": workload_label(w, args.size), "n_sites": n, "storage": "fp64",
+                   "timesteps_per_step": 1,
                    "note": "FP64 CPU oracle, one timestep of the full workload per step"},
         "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": threads, "kind": "oracle",
                          "sample": f"{len(timed)} timesteps of the {args.size}^3 workload "
@@ -668,12 +680,11 @@ def bench_gpu(args):
     if rank == 0:
         step_gbs = bytes_s * N * bundle * args.steps / (ms * 1e-3) / 1e9
         out = {
-            "metric": f"pore-site MLUPS ({prec.upper()} store)", "value": value, "unit": "MLUPS",
+            "metric": METRIC, "value": value, "unit": "MLUPS",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"{w.name}: {args.size}^3 sphere pack, porosity "
-                                   f"{w.porosity:.3f}, z periodic, x/y walls, Sw=0.4 blobs",
+            "config": {"workload": workload_label(w, args.size),
                        "n_sites": N, "storage": prec, "timesteps_per_step": bundle,
                        "analysis_per_step": "fp64 basic analysis (saturation, fluxes, Ca)",
                        "l2": "state larger than L2 (no flush needed)",
