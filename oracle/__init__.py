@@ -16,8 +16,11 @@ Parity status of each oracle function (what pins it, see ``tests/test_oracle_*``
   * full model                      duct Poiseuille series, flat-interface tanh
                                     profile, Laplace law (sigma = 6 alpha),
                                     contact angle cos(theta) = phi_s
-  * reservoir slabs                 parity unpinned (only self-consistency:
-                                    the inlet phase advances)
+  * reservoir slabs                 parity unpinned (checked: the exact reset
+                                    state after every step, saturation rising
+                                    monotonically, the front advancing)
+  * the pins themselves             planted mistakes in copies of this oracle
+                                    each fail a named pin
 """
 from .core import (  # noqa: F401
     Oracle,

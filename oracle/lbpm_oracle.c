@@ -66,8 +66,10 @@
  *
  * Parity status: every function here is pinned by the tests against closed
  * forms, physics or an independent dense implementation, except the
- * reservoir reset, whose parity is unpinned (it has no closed form; it is
- * only checked for self-consistency).
+ * reservoir reset, whose parity is unpinned: the flow it drives has no closed
+ * form, and the tests check only that every slab site holds exactly the reset
+ * state after each step and that injection raises the saturation
+ * monotonically while the displacement front advances.
  */
 #include <math.h>
 #include <stdint.h>
