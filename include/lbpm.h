@@ -321,7 +321,8 @@ lbpm_status lbpm_batch_advance(lbpm_batch* batch, long long nsteps);
 lbpm_status lbpm_batch_measure(lbpm_batch* batch, lbpm_measures* out);
 /* Launch shape: threads per block (128, 256 or 512) and resident blocks per
  * SM of the persistent phase and collide grids (0 = occupancy limit, -1 = no
- * persistent grid: one block per tile, scheduled by the hardware). */
+ * persistent grid: one block per tile, scheduled by the hardware). A new
+ * batch starts at 256 threads and -1 for both kernels. */
 lbpm_status lbpm_batch_set_launch(lbpm_batch* batch, int threads, int blocks_per_sm_phase,
                                   int blocks_per_sm_collide);
 /* Autotuner: times each candidate launch shape over steps_per_candidate

@@ -34,8 +34,12 @@ struct lbpm_batch {
     int n_mtiles = 0;
     bool dirty = true;
     // launch shape
+    // resident blocks per SM of the persistent grids (0 = occupancy limit, -1 =
+    // one block per tile). The default is the autotuner's choice on GB300 for
+    // mixed job sizes in both storages: the hardware block scheduler balances
+    // uneven tiles better than a static round-robin over persistent blocks.
     int bt = 256;
-    int bps[2] = {0, 0};   // resident blocks per SM of the persistent grids (0 = occupancy limit, -1 = one block per tile)
+    int bps[2] = {-1, -1};
     int n_sm = 0;
     // bundle graph (2 timesteps)
     cudaStream_t cap_stream = nullptr;
