@@ -12,7 +12,8 @@ W7 = morph.W7
 T19 = np.array([1 / 3] + [1 / 18] * 6 + [1 / 36] * 12)
 
 
-def _oracle_with_phase(shape, periodic, phi_of_xyz):
+def _oracle_with_phase(shape, periodic, phi_of_xyz, n_of_xyz=None):
+    """Oracle at rest with phase phi and total component density N (default 1)."""
     nz, ny, nx = shape
     lab = np.zeros(shape, np.uint16)
     o = oracle.Oracle(lab, np.zeros(shape, np.float32), periodic, tau_a=0.7, tau_b=0.7, alpha=0.005,
@@ -22,8 +23,9 @@ def _oracle_with_phase(shape, periodic, phi_of_xyz):
     z, r = np.divmod(sv, ny * nx)
     y, x = np.divmod(r, nx)
     phi = phi_of_xyz(x.astype(float), y.astype(float), z.astype(float))
-    A = W7[:, None] * (0.5 * (1 + phi))[None, :]
-    B = W7[:, None] * (0.5 * (1 - phi))[None, :]
+    N = np.ones_like(phi) if n_of_xyz is None else n_of_xyz(x.astype(float), y.astype(float), z.astype(float))
+    A = W7[:, None] * (0.5 * N * (1 + phi))[None, :]
+    B = W7[:, None] * (0.5 * N * (1 - phi))[None, :]
     f = np.repeat(T19[:, None], o.N, axis=1)
     o.set_state(f, A, B, 0)
     return o, x, y, z, phi
@@ -31,7 +33,9 @@ def _oracle_with_phase(shape, periodic, phi_of_xyz):
 
 def test_flat_equilibrium_interface_moves_by_delta():
     x0, delta = 12.3, 0.7
-    o, x, _, _, phi = _oracle_with_phase((4, 4, 24), (0, 1, 1), lambda x, y, z: np.tanh(BETA * (x0 - x)))
+    # a non-uniform total density: the re-initialised sites must keep theirs
+    n_of = lambda x, y, z: 1.0 + 0.03 * np.sin(0.7 * x + 0.3 * y)
+    o, x, y, z, phi = _oracle_with_phase((4, 4, 24), (0, 1, 1), lambda x, y, z: np.tanh(BETA * (x0 - x)), n_of)
     before, after = morph.morph(o, delta, BETA, (0, 1, 1))
     _, A, B = o.state()
     phin = (A.sum(0) - B.sum(0)) / (A.sum(0) + B.sum(0))
@@ -42,7 +46,7 @@ def test_flat_equilibrium_interface_moves_by_delta():
     reach = band | np.array([np.min(np.abs(xb - xi)) <= 4 for xi in x])
     want = np.where(reach, np.tanh(BETA * (x0 + delta - x)), phi)
     assert np.abs(phin - want).max() < 1e-12
-    assert np.abs(A.sum(0) + B.sum(0) - 1.0).max() < 1e-14      # N kept at every site
+    assert np.abs(A.sum(0) + B.sum(0) - n_of(x, y, z)).max() < 1e-14      # N kept at every site
 
 
 def test_one_voxel_of_dilation_adds_one_plane():

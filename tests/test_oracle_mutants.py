@@ -6,9 +6,13 @@ compiles it, and runs the pins that should catch it in a subprocess that
 loads the mutated library (LBPM_ORACLE_LIB). The case passes when at least
 one of those pins fails. The pins named are closed forms, values the paper
 prints, invariants, or the independent dense implementation on tiny inputs.
+The NumPy oracles of shell aggregation and image preparation get the same
+treatment: the subprocess puts a mutated copy of the module in place of the
+original before the pins import it.
 
-Left out on purpose: relaxing a conserved moment (rho, j) is not a mistake
-that changes anything, since its equilibrium equals the moment itself.
+Left out on purpose, because they change nothing: relaxing a conserved
+moment (rho, j), whose equilibrium equals the moment itself, and flipping
+the direction of a shift over a symmetric ball of offsets.
 """
 import os
 import shutil
@@ -99,3 +103,69 @@ def test_planted_mistake_fails_a_pin(source, tmp_path, name, old, new, pins):
     # exit code 1: tests ran and at least one failed; 0 would mean the pins
     # missed the mistake, anything else that they did not run
     assert r.returncode == 1, f"{name}: pins {pins} did not catch it\n{r.stdout[-2000:]}"
+
+
+# (module, name, text, planted replacement, pins expected to catch it)
+PY_MUTANTS = [
+    ("morph", "sign of the shift delta",
+     "-np.tanh(beta * (Phi - delta))", "-np.tanh(beta * (Phi + delta))",
+     "tests/test_oracle_morph.py::test_one_voxel_of_dilation_adds_one_plane"),
+    ("morph", "distance scaled by beta instead of 1/beta",
+     "np.abs(np.arctanh(phi[band])) / beta", "np.abs(np.arctanh(phi[band])) * beta",
+     "tests/test_oracle_morph.py::test_flat_equilibrium_interface_moves_by_delta"),
+    ("morph", "far field by squared distance",
+     "np.sqrt(o[0] ** 2 + o[1] ** 2 + o[2] ** 2) +", "(o[0] ** 2 + o[1] ** 2 + o[2] ** 2) +",
+     "tests/test_oracle_morph.py::test_flat_equilibrium_interface_moves_by_delta"),
+    ("morph", "sign of the far-field distance",
+     "np.where(phi > 0, -best, best)", "np.where(phi > 0, best, -best)",
+     "tests/test_oracle_morph.py::test_relaxed_drop_grows_by_a_shell"),
+    ("morph", "band of the exact distance too narrow",
+     "np.tanh(3.0 * beta)", "np.tanh(1.0 * beta)",
+     "tests/test_oracle_morph.py::test_relaxed_drop_grows_by_a_shell"),
+    ("morph", "re-initialised densities swapped",
+     "na, nb = 0.5 * N * (1 + phin), 0.5 * N * (1 - phin)", "na, nb = 0.5 * N * (1 - phin), 0.5 * N * (1 + phin)",
+     "tests/test_oracle_morph.py::test_flat_equilibrium_interface_moves_by_delta"),
+    ("morph", "site density not kept",
+     "na, nb = 0.5 * N * (1 + phin), 0.5 * N * (1 - phin)", "na, nb = 0.5 * (1 + phin), 0.5 * (1 - phin)",
+     "tests/test_oracle_morph.py::test_flat_equilibrium_interface_moves_by_delta"),
+    ("prepare", "open ball (distance < radius)",
+     "x * x + y * y + z * z <= radius * radius", "x * x + y * y + z * z < radius * radius",
+     "tests/test_oracle_prepare.py::test_ball_sizes_are_lattice_point_counts"),
+    ("prepare", "inlet layers tested against the inlet face",
+     "new = np.where((layer != 0) & (outlet_face == 0), 0, new)",
+     "new = np.where((layer != 0) & (inlet_face == 0), 0, new)",
+     "tests/test_oracle_prepare.py::test_mixing_layer_by_hand"),
+    ("prepare", "one outlet layer too few",
+     "if a >= L - n_mix:", "if a > L - n_mix:",
+     "tests/test_oracle_prepare.py::test_mixing_layer_by_hand"),
+    ("prepare", "pore voxels relabelled too",
+     "out[(lab != 0) & near] = new_label", "out[near] = new_label",
+     "tests/test_oracle_prepare.py::test_relabel_matches_scipy_distance_transform"),
+]
+
+_BOOT = """
+import sys, types
+sys.path.insert(0, {root!r})
+import oracle
+src = open({path!r}).read()
+mod = types.ModuleType("oracle.{name}")
+mod.__file__ = {path!r}
+mod.__package__ = "oracle"
+exec(compile(src, {path!r}, "exec"), mod.__dict__)
+sys.modules["oracle.{name}"] = mod
+setattr(oracle, "{name}", mod)
+import pytest
+sys.exit(pytest.main(["-q", "-x", "-p", "no:cacheprovider", {pins!r}]))
+"""
+
+
+@pytest.mark.parametrize("module,name,old,new,pins", PY_MUTANTS, ids=[m[1] for m in PY_MUTANTS])
+def test_planted_mistake_in_a_numpy_oracle_fails_a_pin(tmp_path, module, name, old, new, pins):
+    with open(os.path.join(ROOT, "oracle", f"{module}.py")) as fh:
+        src = fh.read()
+    assert src.count(old) == 1, f"the text to mutate is not unique: {old!r}"
+    path = tmp_path / f"{module}.py"
+    path.write_text(src.replace(old, new))
+    boot = _BOOT.format(root=ROOT, path=str(path), name=module, pins=pins)
+    r = subprocess.run([sys.executable, "-c", boot], capture_output=True, text=True, cwd=ROOT)
+    assert r.returncode == 1, f"{name}: {pins} did not catch it\n{r.stdout[-2000:]}"
