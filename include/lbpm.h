@@ -90,7 +90,9 @@ typedef struct {
     double tau_a, tau_b;
     double alpha, beta;
     double force[3];
-    int precision;
+    int precision;        /* storage of the distributions: LBPM_FP32, or LBPM_FP16 - each value kept in
+                           * fp16 as its deviation from a local rest state (about half the memory and
+                           * traffic), all arithmetic fp32, the measures fp64 */
     int periodic[3];      /* 1 = periodic axis; a non-periodic face is a solid wall (phi_s = 0) */
     int reservoir_z;      /* 0 none, 1 reservoir slabs, 2 pressure faces, 3 flux inlet + pressure outlet */
     double rho_in, rho_out;
