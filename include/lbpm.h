@@ -304,7 +304,12 @@ lbpm_status lbpm_kernel_timing(lbpm_ctx* ctx, double* ms_collide, long long* n_c
  */
 typedef struct lbpm_batch lbpm_batch;
 
+/* Create an empty batch on CUDA `device`, issuing work on `cuda_stream` (a
+ * cudaStream_t; NULL = the legacy default stream). *out receives it.
+ * Errors: LBPM_E_INVALID (out NULL, bad device), LBPM_E_OOM, LBPM_E_CUDA. */
 lbpm_status lbpm_batch_create(lbpm_batch** out, int device, void* cuda_stream);
+/* Wait for the batch's stream and free its tables; the jobs are not touched
+ * (they stay valid and belong to the caller). NULL is a no-op. */
 lbpm_status lbpm_batch_destroy(lbpm_batch* batch);
 /* Allocator hooks for the batch's own tables (see lbpm_set_allocator). */
 lbpm_status lbpm_batch_set_allocator(lbpm_batch* batch, lbpm_alloc_fn alloc, lbpm_free_fn free_fn, void* user);
@@ -333,6 +338,8 @@ lbpm_status lbpm_batch_set_launch(lbpm_batch* batch, int threads, int blocks_per
  * batch's site count) for the process. Returns the chosen shape. */
 lbpm_status lbpm_batch_tune(lbpm_batch* batch, int steps_per_candidate, int* threads, int* blocks_per_sm_phase,
                             int* blocks_per_sm_collide);
+/* Kernel launches the batch has issued so far (graph replays counted per
+ * kernel node). Errors: LBPM_E_INVALID (NULL argument). */
 lbpm_status lbpm_batch_launch_count(const lbpm_batch* batch, long long* launches);
 
 /*
@@ -400,8 +407,13 @@ typedef struct {
  * steps per round (even). */
 lbpm_status lbpm_server_create(lbpm_server** out, int device, void* cuda_stream, size_t hbm_budget_bytes,
                                int max_jobs, int check_interval);
+/* Free the server, its batch and every job's device state (finished or
+ * not). NULL is a no-op. */
 lbpm_status lbpm_server_destroy(lbpm_server* server);
+/* Allocator hooks for every job and the batch (see lbpm_set_allocator);
+ * LBPM_E_STATE once jobs were submitted. */
 lbpm_status lbpm_server_set_allocator(lbpm_server* server, lbpm_alloc_fn alloc, lbpm_free_fn free_fn, void* user);
+/* Message of the server's last failed call ("" if none; valid until the next call). */
 const char* lbpm_server_last_error(const lbpm_server* server);
 /* Queue a job (LBPM_E_OOM if its footprint exceeds the whole budget). */
 lbpm_status lbpm_server_submit(lbpm_server* server, const lbpm_job_spec* spec, long long* ticket);
