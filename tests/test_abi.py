@@ -1,6 +1,7 @@
 """C-ABI checks that need no GPU.
 
-* the library loads and exports every function include/lbpm.h declares;
+* the library loads and exports every function include/lbpm.h declares, and
+  each declaration carries its comment;
 * the Python binding declares exactly those functions;
 * the ctypes structures match the C layout (sizes and offsets from gcc);
 * without a GPU, lbpm_create fails with a status code instead of crashing,
@@ -40,6 +41,25 @@ def test_header_declares_expected_calls():
                  "lbpm_set_params", "lbpm_init_fluids", "lbpm_advance", "lbpm_measure",
                  "lbpm_read_field", "lbpm_read_distributions", "lbpm_get_index"):
         assert must in names
+
+
+def test_every_declared_call_is_documented():
+    """Each declaration (or group of adjacent declarations) follows a comment
+    that states what the call does and how it fails."""
+    lines = open(HEADER).read().split("\n")
+    decl = re.compile(r"^(lbpm_status|const char\*|int|void|double|long long)\s+\**(lbpm_\w+)\(")
+    undocumented = []
+    for i, line in enumerate(lines):
+        m = decl.match(line)
+        if not m:
+            continue
+        j = i - 1
+        while j >= 0 and decl.match(lines[j]):
+            j -= 1
+        prev = lines[j].strip()
+        if not (prev.endswith("*/") or prev.startswith("*") or prev.startswith("/*")):
+            undocumented.append(m.group(2))
+    assert not undocumented, undocumented
 
 
 def test_every_declared_symbol_is_exported(lib):
