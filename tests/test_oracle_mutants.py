@@ -29,6 +29,7 @@ PHYS = "tests/test_oracle_physics.py::"
 OPS = "tests/test_oracle_ops.py::"
 LAT = "tests/test_oracle_lattice.py::"
 DYN = "tests/test_oracle_dynamics.py::"
+MEAS = "tests/test_oracle_measures.py::"
 
 # (name, text in the oracle, planted replacement, pins expected to catch it)
 MUTANTS = [
@@ -77,6 +78,30 @@ MUTANTS = [
     ("component streamed into the opposite slot",
      "o->An[(long long)t * Q7 + q] = Apost[q];", "o->An[(long long)t * Q7 + opposite(q)] = Apost[q];",
      [DYN + "test_rest_state_is_steady"]),
+    ("reported velocity without the half force",
+     "u[a] = (j[a] + 0.5 * o->F[a]) / RHO0;", "u[a] = j[a] / RHO0;",
+     [MEAS + "test_uniform_flow_of_pure_a"]),
+    ("interfacial tension alpha instead of 6 alpha",
+     "/ (6.0 * o->alpha);", "/ o->alpha;",
+     [MEAS + "test_uniform_flow_of_pure_a"]),
+    ("viscosities of the two fluids swapped",
+     "const double mu_a = RHO0 * (o->tau_a - 0.5) / 3.0, mu_b = RHO0 * (o->tau_b - 0.5) / 3.0;",
+     "const double mu_a = RHO0 * (o->tau_b - 0.5) / 3.0, mu_b = RHO0 * (o->tau_a - 0.5) / 3.0;",
+     [MEAS + "test_two_phases_on_alternating_sites"]),
+    ("phase volume fraction over the pore sites",
+     "ca = ((cnt_a / V) * mu_a * ua + (cnt_b / V) * mu_b * ub)",
+     "ca = ((cnt_a / (double)N) * mu_a * ua + (cnt_b / (double)N) * mu_b * ub)",
+     [MEAS + "test_uniform_flow_of_pure_a"]),
+    ("flux of A weighted by Nb/N",
+     "qa[a] += xa * u[a];", "qa[a] += xb * u[a];",
+     [MEAS + "test_uniform_mixture_splits_by_component_fraction"]),
+    ("Darcy flux over the pore sites instead of the volume",
+     "out[12 + a] = q[a] / V;", "out[12 + a] = q[a] / (double)N;",
+     [MEAS + "test_uniform_flow_of_pure_a"]),
+    ("instability flagged at any negative component density",
+     "if (Na < -1e-2 || Nb < -1e-2 || Nt <= 0.0 || rho <= 0.0) status |= 2;",
+     "if (Na < 0.0 || Nb < 0.0 || Nt <= 0.0 || rho <= 0.0) status |= 2;",
+     [MEAS + "test_instability_flags"]),
 ]
 
 
