@@ -69,7 +69,9 @@
  * reservoir reset, whose parity is unpinned: the flow it drives has no closed
  * form, and the tests check only that every slab site holds exactly the reset
  * state after each step and that injection raises the saturation
- * monotonically while the displacement front advances.
+ * monotonically while the displacement front advances; and the component
+ * population entering at a pressure face (the reservoir fluid's equilibrium at
+ * the face velocity), whose parity is unpinned as well (no closed form).
  */
 #include <math.h>
 #include <stdint.h>

@@ -30,6 +30,7 @@ OPS = "tests/test_oracle_ops.py::"
 LAT = "tests/test_oracle_lattice.py::"
 DYN = "tests/test_oracle_dynamics.py::"
 MEAS = "tests/test_oracle_measures.py::"
+PBC = "tests/test_oracle_pressure_bc.py::"
 
 # (name, text in the oracle, planted replacement, pins expected to catch it)
 MUTANTS = [
@@ -98,6 +99,24 @@ MUTANTS = [
     ("Darcy flux over the pore sites instead of the volume",
      "out[12 + a] = q[a] / V;", "out[12 + a] = q[a] / (double)N;",
      [MEAS + "test_uniform_flow_of_pure_a"]),
+    ("Zou-He normal and edge weights swapped",
+     "(tang ? 1.0 / 6.0 : 1.0 / 3.0)", "(tang ? 1.0 / 3.0 : 1.0 / 6.0)",
+     [PBC + "test_face_sites_hold_the_face_density_and_no_tangential_momentum"]),
+    ("sign of the tangential-momentum correction",
+     "- XI[q][0] * Nt[0] - XI[q][1] * Nt[1];", "+ XI[q][0] * Nt[0] + XI[q][1] * Nt[1];",
+     [PBC + "test_face_sites_hold_the_face_density_and_no_tangential_momentum"]),
+    ("tangential momentum without its 1/2",
+     "Nt[0] *= 0.5;\n        Nt[1] *= 0.5;", "",
+     [PBC + "test_face_sites_hold_the_face_density_and_no_tangential_momentum"]),
+    ("face velocity with the leaving populations once",
+     "const double un = 1.0 - (s0 + 2.0 * sout) / rho;", "const double un = 1.0 - (s0 + sout) / rho;",
+     [PBC + "test_face_sites_hold_the_face_density_and_no_tangential_momentum"]),
+    ("flux inlet density with n_in + Q",
+     "rho_in = K / ((double)n_in - o->flux_in);", "rho_in = K / ((double)n_in + o->flux_in);",
+     [PBC + "test_flux_inlet_carries_exactly_the_prescribed_flux"]),
+    ("flux inlet sum with the leaving populations once",
+     "else if (XI[q][2] < 0) K += 2.0 * g[q];", "else if (XI[q][2] < 0) K += g[q];",
+     [PBC + "test_flux_inlet_carries_exactly_the_prescribed_flux"]),
     ("instability flagged at any negative component density",
      "if (Na < -1e-2 || Nb < -1e-2 || Nt <= 0.0 || rho <= 0.0) status |= 2;",
      "if (Na < 0.0 || Nb < 0.0 || Nt <= 0.0 || rho <= 0.0) status |= 2;",
