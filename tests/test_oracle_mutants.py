@@ -31,6 +31,7 @@ LAT = "tests/test_oracle_lattice.py::"
 DYN = "tests/test_oracle_dynamics.py::"
 MEAS = "tests/test_oracle_measures.py::"
 PBC = "tests/test_oracle_pressure_bc.py::"
+IDX = "tests/test_oracle_index.py::"
 
 # (name, text in the oracle, planted replacement, pins expected to catch it)
 MUTANTS = [
@@ -99,6 +100,15 @@ MUTANTS = [
     ("Darcy flux over the pore sites instead of the volume",
      "out[12 + a] = q[a] / V;", "out[12 + a] = q[a] / (double)N;",
      [MEAS + "test_uniform_flow_of_pure_a"]),
+    ("periodic flag of x applied to every axis",
+     "if (!o->periodic[a]) return 0;", "if (!o->periodic[0]) return 0;",
+     [IDX + "test_index_matches_brute_force"]),
+    ("neighbour table laid out site-major",
+     "o->nbr[(long long)(q - 1) * N + s] = t;", "o->nbr[(long long)s * 18 + (q - 1)] = t;",
+     [IDX + "test_index_matches_brute_force"]),
+    ("affinity of solid voxels lost",
+     "o->phis[v] = affinity ? (double)affinity[v] : 0.0;", "o->phis[v] = 0.0;",
+     [OPS + "test_gradient_sees_affinity_of_solid_neighbour"]),
     ("Zou-He normal and edge weights swapped",
      "(tang ? 1.0 / 6.0 : 1.0 / 3.0)", "(tang ? 1.0 / 3.0 : 1.0 / 6.0)",
      [PBC + "test_face_sites_hold_the_face_density_and_no_tangential_momentum"]),
