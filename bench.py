@@ -91,11 +91,17 @@ def measured_peaks():
 
 
 def kernel_hash(precision: str) -> str:
+    """Hash of the step kernels' source, comments and whitespace left out, so
+    that the recorded DRAM traffic stays tied to the code it was measured on."""
+    import re
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2007_12266_gb300", "csrc")
     for name in ("step_kernels.cuh", "step.cu", "lattice.cuh", "internal.h"):
-        with open(os.path.join(csrc, name), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(csrc, name)) as fh:
+            src = fh.read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", "", src)
+        h.update("".join(src.split()).encode())
     h.update(precision.encode())
     return h.hexdigest()[:16]
 

@@ -73,13 +73,13 @@ struct StoreF32 {
 // (DomainView::phi is double-buffered by step parity) at the upstream voxel
 // x - xi_q, or at its own voxel when that link bounced back (DomainView::wall6),
 // so no neighbour id is looked up for it. The phase pass needs only the sum
-// of the references over the seven directions, Na = sum_q s_q + (sum_q w_q +
-// S)/2 with S = sum_q w_q phi_w(q) (likewise Nb with -S); the collision, which
-// holds those phases for its colour gradient, stores S per site
-// (DomainView::rsum), so the phase pass reads one coalesced number instead of
-// six phases. Against the writer's own (Na, Nb)
-// the stored number gains w_q (N - 1)(1 +- phi_w)/2; N = Na + Nb follows the
-// density, within a few 1e-2 of 1.
+// of the references over the seven directions, Na = sum_q s_q + (1 + S)/2
+// with S = sum_q w_q phi_w(q) (likewise Nb with -S; the writers' rest values
+// absorb the fp32 weights' excess over 1); the collision, which holds those
+// phases for its colour gradient, stores S per site (DomainView::rsum), so the
+// phase pass reads one coalesced number instead of six phases. Against the
+// writer's own (Na, Nb) the stored number gains w_q (N - 1)(1 +- phi_w)/2;
+// N = Na + Nb follows the density, within a few 1e-2 of 1.
 // Storing A, B themselves let every site of a pure phase round the same value
 // the same way on the fp16 grid, a biased error that leaked 3e-3 of the
 // component mass per 1,000 steps; storing f - t_q left the local density
