@@ -32,6 +32,7 @@ DYN = "tests/test_oracle_dynamics.py::"
 MEAS = "tests/test_oracle_measures.py::"
 PBC = "tests/test_oracle_pressure_bc.py::"
 IDX = "tests/test_oracle_index.py::"
+RES = "tests/test_oracle_reservoirs.py::"
 
 # (name, text in the oracle, planted replacement, pins expected to catch it)
 MUTANTS = [
@@ -100,6 +101,19 @@ MUTANTS = [
     ("Darcy flux over the pore sites instead of the volume",
      "out[12 + a] = q[a] / V;", "out[12 + a] = q[a] / (double)N;",
      [MEAS + "test_uniform_flow_of_pure_a"]),
+    ("reservoir slabs one layer thin",
+     "if (z < RESERVOIR_DEPTH) side = 1;", "if (z < RESERVOIR_DEPTH - 1) side = 1;",
+     [RES + "test_slab_sites_hold_the_reset_state_after_every_step"]),
+    ("inlet slab filled with B as well",
+     "B[n * Q7 + q] = side == 1 ? 0.0 : W7[q];", "B[n * Q7 + q] = W7[q];",
+     [RES + "test_slab_sites_hold_the_reset_state_after_every_step"]),
+    ("outlet density in both slabs",
+     "const double rho = side == 1 ? o->rho_in : o->rho_out;", "const double rho = o->rho_out;",
+     [RES + "test_slab_sites_hold_the_reset_state_after_every_step"]),
+    ("initial phases of A and B swapped",
+     "const double Na = 0.5 * (1.0 + p), Nb = 0.5 * (1.0 - p);",
+     "const double Na = 0.5 * (1.0 - p), Nb = 0.5 * (1.0 + p);",
+     [RES + "test_injection_raises_saturation_and_advances_the_front"]),
     ("periodic flag of x applied to every axis",
      "if (!o->periodic[a]) return 0;", "if (!o->periodic[0]) return 0;",
      [IDX + "test_index_matches_brute_force"]),
