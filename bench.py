@@ -739,26 +739,31 @@ def bench_gpu(args):
 
 
 def main():
-    ap = argparse.ArgumentParser()
-    ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
-    ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--mode", default="headline", choices=["headline", "precision", "serving", "prepare"])
-    ap.add_argument("--precision-steps", type=int, default=5000)
-    ap.add_argument("--crop-steps", type=int, default=5000)
-    ap.add_argument("--size", type=int, default=256)
-    ap.add_argument("--bundle", type=int, default=100)
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16"])
-    ap.add_argument("--cpu-steps", type=int, default=20)
-    ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-fp16", action="store_true")
-    ap.add_argument("--no-batched", action="store_true")
-    ap.add_argument("--no-serving", action="store_true")
-    ap.add_argument("--batched-jobs", type=int, default=64)
-    ap.add_argument("--batched-steps", type=int, default=2000)
-    ap.add_argument("--serving-jobs", type=int, default=24)
-    ap.add_argument("--serving-max-steps", type=int, default=4000)
+    ap = argparse.ArgumentParser(description="Pore-site MLUPS of the color-gradient LBM step on GB300 "
+                                             "(one JSON line on stdout)")
+    ap.add_argument("--gpus", type=int, default=1, help="GPUs (launch under torchrun for more than one)")
+    ap.add_argument("--steps", type=int, default=10, help="timed bench steps (one step = --bundle timesteps "
+                                                          "+ the fp64 analysis)")
+    ap.add_argument("--warmup", type=int, default=3, help="untimed warm-up steps")
+    ap.add_argument("--impl", default="native", choices=["native", "reference"],
+                    help="native: the CUDA library; reference: the FP64 oracle on the host cores")
+    ap.add_argument("--mode", default="headline", choices=["headline", "precision", "serving", "prepare"],
+                    help="headline line, 1024^3 FP32 vs FP16 with the oracle crop, full serving trace, "
+                         "or image preparation")
+    ap.add_argument("--precision-steps", type=int, default=5000, help="precision mode: timesteps")
+    ap.add_argument("--crop-steps", type=int, default=5000, help="precision mode: timesteps of the oracle crop")
+    ap.add_argument("--size", type=int, default=256, help="edge of the headline (or precision) sphere pack")
+    ap.add_argument("--bundle", type=int, default=100, help="timesteps per bench step")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16"], help="storage of the headline run")
+    ap.add_argument("--cpu-steps", type=int, default=20, help="timesteps of the oracle's CPU baseline")
+    ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle's CPU baseline")
+    ap.add_argument("--no-fp16", action="store_true", help="skip the FP16-storage run of the headline workload")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched job set")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving run")
+    ap.add_argument("--batched-jobs", type=int, default=64, help="jobs of the batched set")
+    ap.add_argument("--batched-steps", type=int, default=2000, help="timesteps of the batched set")
+    ap.add_argument("--serving-jobs", type=int, default=24, help="arrivals of the serving run")
+    ap.add_argument("--serving-max-steps", type=int, default=4000, help="step ceiling of a serving job")
     args = ap.parse_args()
     if args.impl == "reference":
         return bench_reference(args)
