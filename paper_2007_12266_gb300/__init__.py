@@ -14,6 +14,7 @@ from __future__ import annotations
 
 import atexit
 import ctypes as ct
+import json
 import weakref
 from typing import Optional
 
@@ -22,7 +23,7 @@ import numpy as np
 from . import _lib
 from ._lib import JobSpec, JobStatus, LBPMError, Measures, Params
 
-__all__ = ["Domain", "Batch", "Server", "JOB_KINDS", "JOB_STATES", "LBPMError", "FIELDS", "DISTS", "library_path",
+__all__ = ["Domain", "Batch", "Server", "trace_run", "TRACE_FIELDS", "JOB_KINDS", "JOB_STATES", "LBPMError", "FIELDS", "DISTS", "library_path",
            "version", "force_rescale", "mixing_layer", "mixed_wet_relabel"]
 
 FIELDS = {"phi": 0, "pressure": 1, "ux": 2, "uy": 3, "uz": 4, "na": 5, "nb": 6, "rho": 7}
@@ -86,6 +87,48 @@ def _measures_dict(m: Measures) -> dict:
         v = getattr(m, name)
         out[name] = list(v) if hasattr(v, "__len__") else v
     return out
+
+
+TRACE_FIELDS = ("step", "sat_mass", "sat_count", "flux", "flux_a", "flux_b", "ca", "mass_drift", "status")
+
+
+def trace_run(sim, steps: int, interval: int, path: Optional[str] = None) -> list:
+    """Advance `sim` (a Domain) by `steps` timesteps in chunks of `interval`,
+    taking the basic analysis (Sec. 4) before the first chunk and after each:
+    one row per analysis with the step, both saturations, the Darcy and phase
+    fluxes, the capillary number, the drift of the total component mass
+    (Na + Nb summed over the sites) relative to the first row, and the status.
+    With `path`, the rows are appended to that file as JSON lines. Stops early
+    (after writing the row) when a measure reports an unstable state."""
+    if interval <= 0 or steps < 0:
+        raise ValueError("interval must be > 0 and steps >= 0")
+    rows = []
+    m0 = None
+    done = 0
+    fh = open(path, "a") if path else None
+    try:
+        while True:
+            m = sim.measure()
+            if m0 is None:
+                m0 = m
+            total0 = m0["mass_a"] + m0["mass_b"]
+            row = {"step": int(m["step"]), "sat_mass": m["sat_mass"], "sat_count": m["sat_count"],
+                   "flux": list(m["flux"]), "flux_a": list(m["flux_a"]), "flux_b": list(m["flux_b"]),
+                   "ca": m["ca"],
+                   "mass_drift": (m["mass_a"] + m["mass_b"]) / total0 - 1.0 if total0 else 0.0,
+                   "status": int(m["status"])}
+            rows.append(row)
+            if fh:
+                fh.write(json.dumps(row) + "\n")
+                fh.flush()
+            if row["status"] != 0 or done >= steps:
+                return rows
+            n = min(interval, steps - done)
+            sim.advance(n)
+            done += n
+    finally:
+        if fh:
+            fh.close()
 
 
 def _torch_allocator(torch, device, stream):
@@ -242,6 +285,10 @@ class Domain:
     # -- running ---------------------------------------------------------
     def advance(self, nsteps: int):
         self._check(self._L.lbpm_advance(self._h, int(nsteps)))
+
+    def run_with_trace(self, steps: int, interval: int, path: Optional[str] = None) -> list:
+        """Advance with the basic analysis every `interval` steps (see trace_run)."""
+        return trace_run(self, steps, interval, path)
 
     def sync(self):
         self._check(self._L.lbpm_sync(self._h))
