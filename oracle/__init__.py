@@ -19,6 +19,10 @@ Parity status of each oracle function (what pins it, see ``tests/test_oracle_*``
   * reservoir slabs                 parity unpinned (checked: the exact reset
                                     state after every step, saturation rising
                                     monotonically, the front advancing)
+  * pressure faces, flux inlet      exact face density and zero tangential
+                                    momentum, pressure-driven and flux-driven
+                                    duct series, uniform component density
+                                    between two faces at equal density
   * the pins themselves             planted mistakes in copies of this oracle
                                     each fail a named pin
 """

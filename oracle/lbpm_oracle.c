@@ -69,9 +69,11 @@
  * reservoir reset, whose parity is unpinned: the flow it drives has no closed
  * form, and the tests check only that every slab site holds exactly the reset
  * state after each step and that injection raises the saturation
- * monotonically while the displacement front advances; and the component
+ * monotonically while the displacement front advances. The component
  * population entering at a pressure face (the reservoir fluid's equilibrium at
- * the face velocity), whose parity is unpinned as well (no closed form).
+ * the face velocity) is pinned by a closed form: in a body-force-driven duct
+ * between two faces at the same density, the total component density stays
+ * that density at every site and carries the momentum lattice's mass flux.
  */
 #include <math.h>
 #include <stdint.h>

@@ -135,6 +135,14 @@ MUTANTS = [
     ("face velocity with the leaving populations once",
      "const double un = 1.0 - (s0 + 2.0 * sout) / rho;", "const double un = 1.0 - (s0 + sout) / rho;",
      [PBC + "test_face_sites_hold_the_face_density_and_no_tangential_momentum"]),
+    ("entering component population with the face velocity's sign flipped",
+     "const double eq = W7[qin] * rho * (1.0 + 4.5 * XI[qin][2] * uz);",
+     "const double eq = W7[qin] * rho * (1.0 - 4.5 * XI[qin][2] * uz);",
+     [PBC + "test_entering_component_population_keeps_the_face_density"]),
+    ("entering component population at density 1 instead of the face density",
+     "const double eq = W7[qin] * rho * (1.0 + 4.5 * XI[qin][2] * uz);",
+     "const double eq = W7[qin] * (1.0 + 4.5 * XI[qin][2] * uz);",
+     [PBC + "test_entering_component_population_keeps_the_face_density"]),
     ("flux inlet density with n_in + Q",
      "rho_in = K / ((double)n_in - o->flux_in);", "rho_in = K / ((double)n_in + o->flux_in);",
      [PBC + "test_flux_inlet_carries_exactly_the_prescribed_flux"]),
