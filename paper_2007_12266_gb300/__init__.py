@@ -23,9 +23,10 @@ import numpy as np
 from . import _lib
 from ._lib import JobSpec, JobStatus, LBPMError, Measures, Params
 
-__all__ = ["Domain", "Batch", "Server", "trace_run", "TRACE_FIELDS", "JOB_KINDS", "JOB_STATES", "LBPMError", "FIELDS", "DISTS", "library_path",
+__all__ = ["Domain", "Batch", "Server", "trace_run", "TRACE_FIELDS", "JOB_KINDS", "JOB_STATES", "LBPMError", "FIELDS", "DISTS", "STEP_FORMS", "library_path",
            "version", "force_rescale", "mixing_layer", "mixed_wet_relabel"]
 
+STEP_FORMS = {"auto": 0, "populations": 1}
 FIELDS = {"phi": 0, "pressure": 1, "ux": 2, "uy": 3, "uz": 4, "na": 5, "nb": 6, "rho": 7}
 DISTS = {"f": (0, 19), "a": (1, 7), "b": (2, 7)}
 PRECISION = {"fp32": 0, "fp16": 1}
@@ -286,6 +287,12 @@ class Domain:
     def advance(self, nsteps: int):
         self._check(self._L.lbpm_advance(self._h, int(nsteps)))
 
+    def set_step_form(self, form: str):
+        """How advance() carries the component distributions between the steps
+        of one call: "auto" (per-site component sums inside a call of two or
+        more steps, the default) or "populations" (lbpm_set_step_form)."""
+        self._check(self._L.lbpm_set_step_form(self._h, STEP_FORMS[form]))
+
     def run_with_trace(self, steps: int, interval: int, path: Optional[str] = None) -> list:
         """Advance with the basic analysis every `interval` steps (see trace_run)."""
         return trace_run(self, steps, interval, path)
@@ -409,7 +416,9 @@ class Domain:
 class Batch:
     """Several Domains (same GPU, same storage precision) advanced together by
     one persistent launch per phase over all their sites (lbpm_batch_* ABI).
-    Results are bit-identical to advancing each domain alone."""
+    Results agree with advancing each domain alone to fp32 rounding (the
+    batched kernels are compiled separately, so multiply-add contraction may
+    differ); two batched runs of the same jobs are bit-identical."""
 
     def __init__(self, device: int = 0, stream=None, use_torch_allocator: bool = True):
         torch = _torch()

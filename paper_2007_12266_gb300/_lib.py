@@ -86,6 +86,7 @@ SIGNATURES = {
     "lbpm_set_params": (ct.c_int, [c_ctx_p, ct.POINTER(Params)]),
     "lbpm_init_fluids": (ct.c_int, [c_ctx_p, ct.c_void_p]),
     "lbpm_advance": (ct.c_int, [c_ctx_p, ct.c_longlong]),
+    "lbpm_set_step_form": (ct.c_int, [c_ctx_p, ct.c_int]),
     "lbpm_morph": (ct.c_int, [c_ctx_p, ct.c_double, ct.c_int, ct.POINTER(ct.c_longlong), ct.POINTER(ct.c_longlong)]),
     "lbpm_shell_aggregation": (ct.c_int, [c_ctx_p, ct.c_double, ct.c_longlong, ct.c_int, ct.POINTER(ct.c_double),
                                           ct.POINTER(ct.c_int)]),

@@ -67,6 +67,8 @@ void free_state(lbpm_ctx* c) {
     dfree(c, c->d_drho);
     dfree(c, c->d_phi_alt);
     dfree(c, c->d_rsum);
+    dfree(c, c->d_acc);
+    c->d_acc = nullptr;
     c->d_drho = nullptr;
     c->d_phi_alt = nullptr;
     c->d_rsum = nullptr;
@@ -110,7 +112,8 @@ lbpm_status alloc_state(lbpm_ctx* c) {
     c->d_a = dalloc(c, state_bytes(c, 7));
     c->d_b = dalloc(c, state_bytes(c, 7));
     c->d_nsum = static_cast<float*>(dalloc(c, sizeof(float) * c->N));
-    bool ok = c->d_f && c->d_a && c->d_b && c->d_nsum;
+    c->d_acc = static_cast<unsigned long long*>(dalloc(c, sizeof(unsigned long long) * 2 * c->N));
+    bool ok = c->d_f && c->d_a && c->d_b && c->d_nsum && c->d_acc;
     if (c->params.precision == LBPM_FP16) {
         // the second phase grid starts as a copy of the first (solids, walls
         // and their periodic mirrors are static and the same in both)
@@ -238,6 +241,24 @@ void drop_graphs(lbpm_ctx* c) {
         if (g) cudaGraphExecDestroy(g);
         g = nullptr;
     }
+    for (auto& g : c->sum_graphs) {
+        if (g) cudaGraphExecDestroy(g);
+        g = nullptr;
+    }
+}
+
+// Kinds of timestep: the population form, and the first, middle and last
+// step of a run of the sum form (see lbpm_set_step_form).
+enum StepKind { kStepPop = 0, kStepSumFirst = 1, kStepSumMid = 2, kStepSumLast = 3 };
+
+// The two kernels of one timestep of the given kind.
+cudaError_t launch_step_phase(lbpm_ctx* c, int kind, int par, cudaStream_t s) {
+    if (kind == kStepPop || kind == kStepSumFirst) return launch_phase(c, par, s);
+    return launch_phase_sum(c, par, kind == kStepSumLast, s);
+}
+cudaError_t launch_step_collide(lbpm_ctx* c, int kind, int par, cudaStream_t s) {
+    if (kind == kStepPop || kind == kStepSumLast) return launch_collide(c, par, s);
+    return launch_collide_sum(c, par, kind == kStepSumMid, s);
 }
 
 // One timestep: phase pass, fused collide-stream, reservoir reset.
@@ -249,6 +270,39 @@ cudaError_t enqueue_step(lbpm_ctx* c, int par, cudaStream_t s) {
 }
 
 int kernels_per_step(const lbpm_ctx* c) { return c->n_slab ? 3 : 2; }
+
+// The sum form needs its first step's target sums cleared (the run's later
+// steps clear their own as they consume them).
+cudaError_t clear_sums(lbpm_ctx* c, int par, cudaStream_t s) {
+    return cudaMemsetAsync(c->d_acc + static_cast<size_t>(par) * static_cast<size_t>(c->N), 0,
+                           sizeof(unsigned long long) * static_cast<size_t>(c->N), s);
+}
+
+// Whether lbpm_advance(nsteps) runs in the sum form.
+bool use_sum_form(const lbpm_ctx* c, long long nsteps) {
+    return c->step_form == LBPM_STEP_AUTO && c->n_slab == 0 && nsteps >= 2 && c->d_acc != nullptr;
+}
+
+// Capture `steps` (even) middle timesteps of the sum form, starting at an even step.
+cudaError_t capture_sum_bundle(lbpm_ctx* c, int steps, cudaGraphExec_t* out) {
+    if (!c->cap_stream) {
+        cudaError_t e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return e;
+    }
+    cudaError_t e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return e;
+    cudaError_t el = cudaSuccess;
+    for (int k = 0; k < steps && el == cudaSuccess; ++k) {
+        el = launch_step_phase(c, kStepSumMid, k & 1, c->cap_stream);
+        if (el == cudaSuccess) el = launch_step_collide(c, kStepSumMid, k & 1, c->cap_stream);
+    }
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(c->cap_stream, &g);
+    if (el != cudaSuccess) e = el;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(out, g, 0);
+    if (g) cudaGraphDestroy(g);
+    return e;
+}
 
 // Capture `steps` (even) timesteps starting at an even step into a graph.
 cudaError_t capture_bundle(lbpm_ctx* c, int steps, cudaGraphExec_t* out) {
@@ -369,6 +423,14 @@ lbpm_status lbpm_create(lbpm_ctx** out, int device, void* cuda_stream) {
     e = cudaSetDevice(device);
     if (e != cudaSuccess) {
         g_create_error = cudaGetErrorString(e);
+        return LBPM_E_CUDA;
+    }
+    // set-up of the allocation-free field read on this device (its static
+    // staging array is placed now, not inside a later call)
+    e = lbm::noalloc_setup(device);
+    if (e != cudaSuccess) {
+        g_create_error = std::string("allocation-free read set-up: ") + cudaGetErrorString(e);
+        cudaGetLastError();
         return LBPM_E_CUDA;
     }
     lbpm_ctx* c = new (std::nothrow) lbpm_ctx();
@@ -553,12 +615,83 @@ lbpm_status lbpm_init_fluids(lbpm_ctx* c, const float* phi0) {
     return LBPM_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// One plain timestep of the given kind, with CUDA events around its two
+// kernels when kernel timing is on.
+lbpm_status plain_step(lbpm_ctx* c, int kind) {
+    const int par = static_cast<int>(c->step & 1);
+    int e0 = -1, e1 = -1, e2 = -1, e3 = -1;
+    if (c->timing) {
+        e0 = next_event(c);
+        e1 = next_event(c);
+        e2 = next_event(c);
+        e3 = next_event(c);
+    }
+    if (e0 >= 0) cudaEventRecord(c->ev_pool[e0], c->stream);
+    LBPM_CK(c, launch_step_phase(c, kind, par, c->stream));
+    if (e1 >= 0) cudaEventRecord(c->ev_pool[e1], c->stream);
+    if (e2 >= 0) cudaEventRecord(c->ev_pool[e2], c->stream);
+    LBPM_CK(c, launch_step_collide(c, kind, par, c->stream));
+    if (e3 >= 0) cudaEventRecord(c->ev_pool[e3], c->stream);
+    if (e0 >= 0 && e1 >= 0) c->ev_phase.emplace_back(e0, e1);
+    if (e2 >= 0 && e3 >= 0) c->ev_collide.emplace_back(e2, e3);
+    c->launches += 2;
+    c->step += 1;
+    return LBPM_OK;
+}
+
+// lbpm_advance in the sum form (nsteps >= 2, no reservoirs): the first step
+// reads the populations, the middle steps carry the components as per-site
+// sums (replayed from CUDA graphs in bundles of 16 and 2), the last step
+// writes the populations again.
+lbpm_status advance_sum(lbpm_ctx* c, long long nsteps) {
+    LBPM_CK(c, clear_sums(c, static_cast<int>((c->step + 1) & 1), c->stream));
+    lbpm_status st = plain_step(c, kStepSumFirst);
+    if (st) return st;
+    long long mid = nsteps - 2;
+    if (!c->timing && c->use_graphs) {
+        if ((c->step & 1) && mid > 0) {
+            if ((st = plain_step(c, kStepSumMid))) return st;
+            --mid;
+        }
+        const int sizes[2] = {2, 16};
+        for (int gi = 1; gi >= 0; --gi) {
+            while (mid >= sizes[gi]) {
+                if (!c->sum_graphs[gi]) LBPM_CK(c, capture_sum_bundle(c, sizes[gi], &c->sum_graphs[gi]));
+                LBPM_CK(c, cudaGraphLaunch(c->sum_graphs[gi], c->stream));
+                c->launches += 2LL * sizes[gi];
+                c->step += sizes[gi];
+                mid -= sizes[gi];
+            }
+        }
+    }
+    for (; mid > 0; --mid)
+        if ((st = plain_step(c, kStepSumMid))) return st;
+    return plain_step(c, kStepSumLast);
+}
+
+}  // namespace
+
+extern "C" {
+
+lbpm_status lbpm_set_step_form(lbpm_ctx* c, int form) {
+    if (!c) return LBPM_E_INVALID;
+    c->err.clear();
+    if (form != LBPM_STEP_AUTO && form != LBPM_STEP_POPULATIONS) return fail(c, LBPM_E_INVALID, "unknown step form");
+    c->step_form = form;
+    return LBPM_OK;
+}
+
 lbpm_status lbpm_advance(lbpm_ctx* c, long long nsteps) {
     lbpm_status s = enter(c);
     if (s) return s;
     if (nsteps < 0) return fail(c, LBPM_E_INVALID, "nsteps must be >= 0");
     if (!c->have_fluids) return fail(c, LBPM_E_STATE, "initialise the fluids first");
     if (c->unstable) return fail(c, LBPM_E_UNSTABLE, "the state was flagged unstable; re-initialise or restore");
+    if (use_sum_form(c, nsteps)) return advance_sum(c, nsteps);
     long long k = 0;
     if (!c->timing && c->use_graphs) {
         // an odd start takes one plain step, then whole bundles run as graphs

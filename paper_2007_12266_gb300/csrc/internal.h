@@ -39,6 +39,8 @@ struct DomainView {
     void* f;               // [19][N] momentum distributions (AA in place)
     void* a;               // [7][N]  component A
     void* b;               // [7][N]  component B
+    unsigned long long* acc[2];  // [N] sum form: packed fixed-point (Na, Nb) of each site at the step of
+                                 //     parity p, accumulated by the previous collision (see pack_sums)
     float tau_a, tau_b, alpha, beta;
     float fx, fy, fz;
     float fterm[9];        // 3 t_q xi_q . F of the odd directions q = 2k + 1 (forcing term per pair), in
@@ -90,6 +92,8 @@ struct lbpm_ctx {
     void* d_f = nullptr;
     void* d_a = nullptr;
     void* d_b = nullptr;
+    unsigned long long* d_acc = nullptr;   // [2N] sum form: packed component sums by step parity
+    int step_form = LBPM_STEP_AUTO;        // lbpm_set_step_form
     int* d_slab_site = nullptr;     // reservoir sites
     signed char* d_slab_side = nullptr;
     long long n_slab = 0;
@@ -100,9 +104,11 @@ struct lbpm_ctx {
     long long step = 0;
     long long launches = 0;
     int block = 256;
-    // captured step bundles: graphs[0] = 2 timesteps, graphs[1] = 16 timesteps
+    // captured step bundles: graphs[0] = 2 timesteps, graphs[1] = 16 timesteps (population form);
+    // sum_graphs[0] / [1]: 2 / 16 middle timesteps of the sum form
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t graphs[2] = {nullptr, nullptr};
+    cudaGraphExec_t sum_graphs[2] = {nullptr, nullptr};
     bool use_graphs = true;
     // kernel timing
     bool timing = false;
@@ -131,11 +137,22 @@ cudaError_t launch_slab_scatter(const lbpm_ctx* c, const int* flags, const int* 
 cudaError_t launch_export_index(const lbpm_ctx* c, long long* site2vox, int* nbr, cudaStream_t s);
 cudaError_t launch_wall_mask(const lbpm_ctx* c, cudaStream_t s);
 
+// Look up (once per device, with that device current) the device address of
+// the static staging array of lbpm_read_field_noalloc; called by lbpm_create.
+cudaError_t noalloc_setup(int device);
+
 DomainView make_view(const lbpm_ctx* c);
 cudaError_t launch_init_fluids(const lbpm_ctx* c, const float* phi0, cudaStream_t s);
 cudaError_t launch_ref_sum(const lbpm_ctx* c, int parity, cudaStream_t s);
 cudaError_t launch_phase(const lbpm_ctx* c, int parity, cudaStream_t s);
 cudaError_t launch_collide(const lbpm_ctx* c, int parity, cudaStream_t s);
+// Sum form of a timestep (components carried as per-site sums, see pack_sums):
+// phase pass from the sums (write_nsum: also Na + Nb for a population-form
+// collision), and the collision scattering its recolored values into the
+// receivers' sums (from_sums: the site's own Na, Nb come from its sums,
+// otherwise from the phase pass of the population form).
+cudaError_t launch_phase_sum(const lbpm_ctx* c, int parity, bool write_nsum, cudaStream_t s);
+cudaError_t launch_collide_sum(const lbpm_ctx* c, int parity, bool from_sums, cudaStream_t s);
 cudaError_t launch_reservoir(const lbpm_ctx* c, int parity, cudaStream_t s);
 // flux inlet: blocks of the fixed-order face reduction
 constexpr int kFaceBlocks = 64;

@@ -11,7 +11,9 @@
 //
 // The array holds LBPM_NOALLOC_FIELD_MAX_VOXELS floats (8 MiB). Every GPU on
 // which the library's module for this file is loaded keeps it until the
-// process exits. All calls on a device share it and it keeps the last call's
+// process exits. lbpm_create looks up its device address (noalloc_setup), which
+// also loads this file's module on that device, so the array is placed during
+// set-up and not inside a later allocation-free call. All calls on a device share it and it keeps the last call's
 // contents; each call overwrites every entry it reads back (solids with NaN,
 // pores with the field), so nothing stale is returned, but two calls whose
 // device work overlaps (on different streams or host threads) race on it.
@@ -55,6 +57,15 @@ lbpm_status fail_cuda(lbpm_ctx* c, const char* what, cudaError_t e) {
 
 }  // namespace
 
+namespace lbm {
+
+cudaError_t noalloc_setup(int device) {
+    float* p = nullptr;
+    return scratch_on_device(device, &p);
+}
+
+}  // namespace lbm
+
 extern "C" lbpm_status lbpm_read_field_noalloc(lbpm_ctx* c, int which, float* out_dense) {
     if (!c) return LBPM_E_INVALID;
     c->err.clear();
@@ -67,6 +78,7 @@ extern "C" lbpm_status lbpm_read_field_noalloc(lbpm_ctx* c, int which, float* ou
         return fail(c, LBPM_E_INVALID,
                     "image has " + std::to_string(c->V) + " voxels; the allocation-free field read holds at most " +
                         std::to_string(kMaxVoxels) + " (use lbpm_read_field)");
+    // resolved by lbpm_create (noalloc_setup); this only reads the cached address
     float* scratch = nullptr;
     e = scratch_on_device(c->device, &scratch);
     if (e != cudaSuccess) return fail_cuda(c, "cudaGetSymbolAddress(field scratch)", e);

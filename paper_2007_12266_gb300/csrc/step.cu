@@ -30,15 +30,23 @@ __global__ void __launch_bounds__(kBlock) k_phase(DomainView d) {
     phase_thread<PAR, S>(d, t);
 }
 
-template <int PAR, class S>
+template <int PAR, bool WRITE_N>
+__global__ void __launch_bounds__(kBlock) k_phase_sum(DomainView d) {
+    const int t = blockIdx.x * kBlock + threadIdx.x;
+    phase_sum_thread<PAR, WRITE_N>(d, t);
+}
+
+// CF: component form of the collision (see collide_site)
+template <int PAR, class S, int CF>
 __global__ void __launch_bounds__(kBlock, 4) k_collide(DomainView d) {
-    // odd steps: slot (and fp16 reference) cache, see SlotCache
-    constexpr int kSlots = PAR == 1 ? (Q19 - 1) * kBlock : 1;
+    // odd steps: slot (and fp16 reference) cache, see SlotCache; even steps of
+    // the sum form: the six face neighbours
+    constexpr int kSlots = PAR == 1 ? (Q19 - 1) * kBlock : (CF != 0 ? (Q7 - 1) * kBlock : 1);
     constexpr int kRefs = PAR == 1 && S::kRef ? (Q19 - 1) * kBlock : 1;
     __shared__ int slot[kSlots];
     __shared__ float ref[kRefs];
     const int n = blockIdx.x * kBlock + threadIdx.x;
-    if (n < d.n_sites) collide_thread<PAR, S>(d, n, SlotCache{slot + threadIdx.x, ref + threadIdx.x, kBlock});
+    if (n < d.n_sites) collide_thread<PAR, S, CF>(d, n, SlotCache{slot + threadIdx.x, ref + threadIdx.x, kBlock});
 }
 
 template <int PAR, class S>
@@ -188,6 +196,8 @@ DomainView make_view(const lbpm_ctx* c) {
     d.f = c->d_f;
     d.a = c->d_a;
     d.b = c->d_b;
+    d.acc[0] = c->d_acc;
+    d.acc[1] = c->d_acc ? c->d_acc + c->N : nullptr;
     const lbpm_params& p = c->params;
     d.tau_a = static_cast<float>(p.tau_a);
     d.tau_b = static_cast<float>(p.tau_b);
@@ -247,8 +257,31 @@ cudaError_t launch_collide(const lbpm_ctx* c, int parity, cudaStream_t s) {
     if (g == 0) return cudaSuccess;
     const bool h = c->params.precision == LBPM_FP16;
     if (parity == 0)
-        return h ? launch_pdl(k_collide<0, StoreF16>, g, s, d) : launch_pdl(k_collide<0, StoreF32>, g, s, d);
-    return h ? launch_pdl(k_collide<1, StoreF16>, g, s, d) : launch_pdl(k_collide<1, StoreF32>, g, s, d);
+        return h ? launch_pdl(k_collide<0, StoreF16, 0>, g, s, d) : launch_pdl(k_collide<0, StoreF32, 0>, g, s, d);
+    return h ? launch_pdl(k_collide<1, StoreF16, 0>, g, s, d) : launch_pdl(k_collide<1, StoreF32, 0>, g, s, d);
+}
+
+cudaError_t launch_phase_sum(const lbpm_ctx* c, int parity, bool write_nsum, cudaStream_t s) {
+    DomainView d = make_view(c);
+    const unsigned g = blocks_for(c->N + c->H);
+    if (g == 0) return cudaSuccess;
+    if (parity == 0) return write_nsum ? launch_pdl(k_phase_sum<0, true>, g, s, d) : launch_pdl(k_phase_sum<0, false>, g, s, d);
+    return write_nsum ? launch_pdl(k_phase_sum<1, true>, g, s, d) : launch_pdl(k_phase_sum<1, false>, g, s, d);
+}
+
+cudaError_t launch_collide_sum(const lbpm_ctx* c, int parity, bool from_sums, cudaStream_t s) {
+    DomainView d = make_view(c);
+    const unsigned g = blocks_for(c->N);
+    if (g == 0) return cudaSuccess;
+    const bool h = c->params.precision == LBPM_FP16;
+    if (from_sums) {
+        if (parity == 0)
+            return h ? launch_pdl(k_collide<0, StoreF16, 2>, g, s, d) : launch_pdl(k_collide<0, StoreF32, 2>, g, s, d);
+        return h ? launch_pdl(k_collide<1, StoreF16, 2>, g, s, d) : launch_pdl(k_collide<1, StoreF32, 2>, g, s, d);
+    }
+    if (parity == 0)
+        return h ? launch_pdl(k_collide<0, StoreF16, 1>, g, s, d) : launch_pdl(k_collide<0, StoreF32, 1>, g, s, d);
+    return h ? launch_pdl(k_collide<1, StoreF16, 1>, g, s, d) : launch_pdl(k_collide<1, StoreF32, 1>, g, s, d);
 }
 
 // parity = parity of the step that will READ the reset values; reservoir slabs

@@ -146,6 +146,43 @@ __device__ __forceinline__ void wait_prior_grid() { asm volatile("griddepcontrol
 __device__ __forceinline__ void allow_next_grid() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
 // ---------------------------------------------------------------------------
+// sum form: component densities carried as per-site fixed-point sums
+// ---------------------------------------------------------------------------
+// The recolored populations of Eqs. LBE-mass-a/b are a function of the
+// writing site's Na, Nb, velocity and colour normal, and the next step uses
+// the populations a site receives only through their sums Na, Nb. In the sum
+// form the collision adds each recolored value A*_q, B*_q straight into the
+// sums of the site that receives it (x + xi_q, or x itself on a bounce-back
+// link). A site's (Na, Nb) is one 64-bit word: Na in the high and Nb in the
+// low 32 bits, each in units of 2^-28 (|N| < 8). Adding packed words adds both
+// halves exactly as long as the low sum stays within 32 bits, and integer sums
+// do not depend on the order of the additions, so the result is deterministic
+// and each component's mass is conserved exactly.
+constexpr float kSumOne = 268435456.0f;          // 2^28
+constexpr float kSumInv = 1.0f / 268435456.0f;
+
+__device__ __forceinline__ unsigned long long pack_sums(int a, int b) {
+    return (static_cast<unsigned long long>(static_cast<unsigned>(a)) << 32) +
+           static_cast<unsigned long long>(static_cast<long long>(b));
+}
+__device__ __forceinline__ void unpack_sums(unsigned long long s, int& a, int& b) {
+    b = static_cast<int>(static_cast<unsigned>(s));
+    a = static_cast<int>((static_cast<long long>(s) - static_cast<long long>(b)) >> 32);
+}
+// N = Na + Nb and phi = (Na - Nb)/(Na + Nb) of a site from its sums; the phase
+// pass and the collision both use this function, so they agree bit for bit.
+__device__ __forceinline__ void sums_phase(int a, int b, float& Nt, float& phi) {
+    const long long nt = static_cast<long long>(a) + b;
+    const long long dd = static_cast<long long>(a) - b;
+    const float ntf = static_cast<float>(nt);
+    Nt = ntf * kSumInv;
+    phi = nt > 0 ? static_cast<float>(dd) / ntf : 0.0f;
+}
+__device__ __forceinline__ void red_add(unsigned long long* p, unsigned long long v) {
+    asm volatile("red.relaxed.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// ---------------------------------------------------------------------------
 // AA read map: where the value of direction Q of site n lives at a step of
 // parity PAR (the same slot the step writes direction opp(Q) to).
 // ---------------------------------------------------------------------------
@@ -301,9 +338,42 @@ __device__ __forceinline__ void phase_thread(const DomainView& d, int t) {
     }
 }
 
+// Phase pass of the sum form: phi (and, for a population-form collision
+// next, N) from the site's component sums. Ordering as in phase_thread: the
+// sums were completed by the collision before the previous phase pass.
+template <int PAR, bool WRITE_N>
+__device__ __forceinline__ void phase_sum_thread(const DomainView& d, int t) {
+    int n = -1, dst = -1;
+    if (t < d.n_sites) {
+        n = t;
+    } else if (t < d.n_sites + d.n_halo) {
+        n = __ldg(d.halo_site + (t - d.n_sites));
+        dst = __ldg(d.halo_dst + (t - d.n_sites));
+    }
+    int v = 0;
+    if (n >= 0 && dst < 0) v = __ldg(d.site_vox + n);
+    wait_prior_grid();
+    allow_next_grid();
+    if (n < 0) return;
+    int a, b;
+    unpack_sums(d.acc[PAR][n], a, b);
+    float Nt, phi;
+    sums_phase(a, b, Nt, phi);
+    if (dst < 0) {
+        d.phi[PAR][v] = phi;
+        if constexpr (WRITE_N) d.nsum[n] = Nt;
+    } else {
+        d.phi[PAR][dst] = phi;    // halo voxel of a periodic face
+    }
+}
+
 // ---------------------------------------------------------------------------
 // fused collide + stream                                            Sec. 3.1
 // ---------------------------------------------------------------------------
+// Component forms of the collision (CF): 0 stores the recolored populations
+// (AA slots); 1 and 2 add them into the receivers' sums (sum form), with the
+// site's own Na, Nb taken from the phase pass (1, first step of a run) or
+// from its own sums (2).
 // At an odd step site n reads direction opp(q) from, and writes direction q
 // to, the same slot: row q at the downstream neighbour x + xi_q, or row
 // opp(q) at n itself when that voxel is solid. With fp16 storage both also
@@ -314,6 +384,7 @@ __device__ __forceinline__ void phase_thread(const DomainView& d, int t) {
 // that a warp's accesses fall in distinct banks.
 struct SlotCache {
     int* slot;      // entry of direction 1 of this thread; direction q at slot[(q - 1) * stride]
+                    // (even steps of the sum form: the face neighbour's site id, -1 if solid)
     float* ref;     // same layout (fp16 storage only)
     int stride;     // threads per block
 };
@@ -398,9 +469,11 @@ __device__ __forceinline__ Moments moments(const float (&f)[Q19]) {
 // deviations f and their moments, its phase phi_c, Na, Nb and the colour
 // gradient.
 // Nt: Na + Nb from the phase pass (Na = Nt (1 + phi_c)/2, Nb = Nt (1 - phi_c)/2).
-template <int PAR, class S>
+// a_own, b_own (CF == 2): the site's component sums in fixed point.
+template <int PAR, class S, int CF = 0>
 __device__ __forceinline__ void collide_site(const DomainView& d, int n, const float (&f)[Q19], Moments mo,
-                                             float phi_c, float Nt, float Cx, float Cy, float Cz, SlotCache sc) {
+                                             float phi_c, float Nt, int a_own, int b_own, float Cx, float Cy,
+                                             float Cz, SlotCache sc) {
     using T = typename S::T;
     const size_t N = static_cast<size_t>(d.n_sites);
     T* const F = static_cast<T*>(d.f);
@@ -525,9 +598,51 @@ __device__ __forceinline__ void collide_site(const DomainView& d, int n, const f
     // w_q Na (4.5 u.xi + beta Nb/N n.xi), plus w_q times
     //   Na - (1 + phi_c)/2 = (N - 1)(1 + phi_c)/2   (likewise for Nb).
     // (working units: Na, Nb times K, j divided by K back to u)
+    const float NaK = (0.5f * K) * Nt * (1.0f + phi_c), NbK = (0.5f * K) * Nt * (1.0f - phi_c);
+    if constexpr (CF != 0) {
+        // Sum form: A*_q = w_q Na [1 + 4.5 u.xi_q + beta (Nb/N) n.xi_q] (likewise B*_q)
+        // in fixed point, added into the sums of the site that receives it; the
+        // rest value takes the remainder of the site's own Na (Nb), so the seven
+        // values add up to it exactly.
+        constexpr float kFix = kSumOne / K;   // working units -> fixed point
+        int ra = a_own, rb = b_own;
+        if constexpr (CF == 1) {
+            ra = __float2int_rn(NaK * kFix);
+            rb = __float2int_rn(NbK * kFix);
+        }
+        unsigned long long* const acc = d.acc[PAR ^ 1];
+        static_for<1, Q7>([&](auto qc) {
+            constexpr int q = decltype(qc)::value;
+            float ux = 0.0f, nn = 0.0f;
+            if constexpr (cx(q) != 0) { ux = cx(q) * jx; nn = cx(q) * nx; }
+            if constexpr (cy(q) != 0) { ux = cy(q) * jy; nn = cy(q) * ny; }
+            if constexpr (cz(q) != 0) { ux = cz(q) * jz; nn = cz(q) * nz; }
+            const float base = fmaf(4.5f * iK, ux, 1.0f);
+            const int ia = __float2int_rn(w7(q) * NaK * (base + bxa * nn) * kFix);
+            const int ib = __float2int_rn(w7(q) * NbK * (base - bxb * nn) * kFix);
+            ra -= ia;
+            rb -= ib;
+            // receiver: x + xi_q if it is a pore site, else x itself (bounce-back)
+            int m;
+            if constexpr (PAR == 0) {
+                m = sc.slot[(q - 1) * sc.stride];
+            } else {
+                const int sl = sc.slot[(q - 1) * sc.stride];
+                m = static_cast<unsigned>(sl) < static_cast<unsigned>(d.n_sites) ? sl : -1;
+            }
+            if (m >= 0) {
+                red_add(acc + m, pack_sums(ia, ib));
+            } else {
+                ra += ia;
+                rb += ib;
+            }
+        });
+        red_add(acc + n, pack_sums(ra, rb));
+        d.acc[PAR][n] = 0ull;    // this step's sums are consumed: they receive the step after next
+        return;
+    }
     T* const A = static_cast<T*>(d.a);
     T* const B = static_cast<T*>(d.b);
-    const float NaK = (0.5f * K) * Nt * (1.0f + phi_c), NbK = (0.5f * K) * Nt * (1.0f - phi_c);
     // fp16 only: K (N - 1)(1 +- phi_c)/2, the offsets of the references
     const float hN = (0.5f * K) * (Nt - 1.0f);
     const float eA = hN * (1.0f + phi_c), eB = hN * (1.0f - phi_c);
@@ -575,24 +690,41 @@ __device__ __forceinline__ void collide_site(const DomainView& d, int n, const f
 }
 
 // One site per thread, direct loads.
-template <int PAR, class S>
+template <int PAR, class S, int CF = 0>
 __device__ __forceinline__ void collide_thread(const DomainView& d, int n, SlotCache sc) {
     const int v = __ldg(d.site_vox + n);
     float f[Q19];
     load_f<PAR, S>(d, n, v, f, sc);
+    if constexpr (CF != 0 && PAR == 0) {
+        // sum form, even step: the face neighbours that receive the component values
+        static_for<1, Q7>([&](auto qc) {
+            constexpr int q = decltype(qc)::value;
+            sc.slot[(q - 1) * sc.stride] = __ldg(d.vsite + v + stencil_off(d, q));
+        });
+    }
+    // sum form from the sums: the site's own Na, Nb (complete before the
+    // previous phase pass, like f)
+    int a_own = 0, b_own = 0;
+    if constexpr (CF == 2) unpack_sums(d.acc[PAR][n], a_own, b_own);
 
-    // Everything above (site and neighbour ids, f from the previous collision)
-    // is safe to read before the phase pass of this step completes; phi and
-    // nsum are its outputs, and the A/B slots written below are its inputs.
+    // Everything above (site and neighbour ids, f and the sums from the
+    // previous collision) is safe to read before the phase pass of this step
+    // completes; phi and nsum are its outputs, and the A/B slots written below
+    // are its inputs.
     allow_next_grid();
     wait_prior_grid();
 
     const float* pv = d.phi[PAR] + v;
-    const float phi_c = *pv;
-    const float Nt = d.nsum[n];
+    float phi_c, Nt;
+    if constexpr (CF == 2) {
+        sums_phase(a_own, b_own, Nt, phi_c);
+    } else {
+        phi_c = *pv;
+        Nt = d.nsum[n];
+    }
     float Cx, Cy, Cz;
     color_gradient([&](auto qc) { return pv[stencil_off(d, decltype(qc)::value)]; }, Cx, Cy, Cz);
-    if constexpr (S::kRef) {
+    if constexpr (S::kRef && CF == 0) {
         // references of the values the next phase pass reads at this site: the
         // phase of x - xi_q, which this step writes, or this site's own on a
         // bounce-back link; every face direction has the same weight
@@ -604,7 +736,7 @@ __device__ __forceinline__ void collide_thread(const DomainView& d, int n, SlotC
         });
         d.rsum[n] = fmaf(w7(1), Sf, w7(0) * phi_c);
     }
-    collide_site<PAR, S>(d, n, f, moments(f), phi_c, Nt, Cx, Cy, Cz, sc);
+    collide_site<PAR, S, CF>(d, n, f, moments(f), phi_c, Nt, a_own, b_own, Cx, Cy, Cz, sc);
 }
 
 // ---------------------------------------------------------------------------
