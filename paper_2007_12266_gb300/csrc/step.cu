@@ -30,10 +30,11 @@ __global__ void __launch_bounds__(kBlock) k_phase(DomainView d) {
     phase_thread<PAR, S>(d, t);
 }
 
+constexpr int kPhaseSumPer = 4;   // entries per thread of the sum-form phase pass
+
 template <int PAR, bool WRITE_N>
 __global__ void __launch_bounds__(kBlock) k_phase_sum(DomainView d) {
-    const int t = blockIdx.x * kBlock + threadIdx.x;
-    phase_sum_thread<PAR, WRITE_N>(d, t);
+    phase_sum_thread<PAR, WRITE_N, kPhaseSumPer>(d, blockIdx.x * kBlock * kPhaseSumPer + threadIdx.x, kBlock);
 }
 
 // CF: component form of the collision (see collide_site)
@@ -263,7 +264,7 @@ cudaError_t launch_collide(const lbpm_ctx* c, int parity, cudaStream_t s) {
 
 cudaError_t launch_phase_sum(const lbpm_ctx* c, int parity, bool write_nsum, cudaStream_t s) {
     DomainView d = make_view(c);
-    const unsigned g = blocks_for(c->N + c->H);
+    const unsigned g = blocks_for((c->N + c->H + kPhaseSumPer - 1) / kPhaseSumPer);
     if (g == 0) return cudaSuccess;
     if (parity == 0) return write_nsum ? launch_pdl(k_phase_sum<0, true>, g, s, d) : launch_pdl(k_phase_sum<0, false>, g, s, d);
     return write_nsum ? launch_pdl(k_phase_sum<1, true>, g, s, d) : launch_pdl(k_phase_sum<1, false>, g, s, d);

@@ -178,8 +178,30 @@ __device__ __forceinline__ void sums_phase(int a, int b, float& Nt, float& phi) 
     Nt = ntf * kSumInv;
     phi = nt > 0 ? static_cast<float>(dd) / ntf : 0.0f;
 }
-__device__ __forceinline__ void red_add(unsigned long long* p, unsigned long long v) {
-    asm volatile("red.relaxed.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+// The sums and the site -> voxel map (8 + 4 bytes per site, read by the phase
+// pass and again by the collision) are accessed with an L2 evict-last policy,
+// so that they stay in L2 between the two kernels while the populations
+// stream through it.
+__device__ __forceinline__ unsigned long long l2_keep() {
+    unsigned long long pol;
+    asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+__device__ __forceinline__ void red_add(unsigned long long* p, unsigned long long v, unsigned long long pol) {
+    asm volatile("red.relaxed.gpu.global.add.L2::cache_hint.u64 [%0], %1, %2;" ::"l"(p), "l"(v), "l"(pol) : "memory");
+}
+__device__ __forceinline__ unsigned long long ld_keep(const unsigned long long* p, unsigned long long pol) {
+    unsigned long long v;
+    asm volatile("ld.global.L2::cache_hint.u64 %0, [%1], %2;" : "=l"(v) : "l"(p), "l"(pol) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_keep(unsigned long long* p, unsigned long long v, unsigned long long pol) {
+    asm volatile("st.global.L2::cache_hint.u64 [%0], %1, %2;" ::"l"(p), "l"(v), "l"(pol) : "memory");
+}
+__device__ __forceinline__ int ldg_keep(const int* p, unsigned long long pol) {
+    int v;
+    asm("ld.global.nc.L2::cache_hint.s32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol));
+    return v;
 }
 
 // ---------------------------------------------------------------------------
@@ -339,31 +361,50 @@ __device__ __forceinline__ void phase_thread(const DomainView& d, int t) {
 }
 
 // Phase pass of the sum form: phi (and, for a population-form collision
-// next, N) from the site's component sums. Ordering as in phase_thread: the
-// sums were completed by the collision before the previous phase pass.
-template <int PAR, bool WRITE_N>
-__device__ __forceinline__ void phase_sum_thread(const DomainView& d, int t) {
-    int n = -1, dst = -1;
-    if (t < d.n_sites) {
-        n = t;
-    } else if (t < d.n_sites + d.n_halo) {
-        n = __ldg(d.halo_site + (t - d.n_sites));
-        dst = __ldg(d.halo_dst + (t - d.n_sites));
+// next, N) from the site's component sums, for PER entries per thread
+// (entries t0 + k * stride: sites, then periodic halo voxels). It also clears
+// the sums that this step's collision accumulates into (nobody reads them:
+// their last readers were the previous step's kernels). Ordering as in
+// phase_thread: the sums were completed by the collision before the previous
+// phase pass. Several entries per thread put more loads in flight (one entry
+// per thread left this pass latency-bound at a third of the DRAM bandwidth).
+template <int PAR, bool WRITE_N, int PER>
+__device__ __forceinline__ void phase_sum_thread(const DomainView& d, int t0, int stride) {
+    const unsigned long long pol = l2_keep();
+    int n[PER], dst[PER], v[PER];
+    #pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        const int t = t0 + k * stride;
+        n[k] = -1;
+        dst[k] = -1;
+        v[k] = 0;
+        if (t < d.n_sites) {
+            n[k] = t;
+            v[k] = ldg_keep(d.site_vox + t, pol);
+        } else if (t < d.n_sites + d.n_halo) {
+            n[k] = __ldg(d.halo_site + (t - d.n_sites));
+            dst[k] = __ldg(d.halo_dst + (t - d.n_sites));
+        }
     }
-    int v = 0;
-    if (n >= 0 && dst < 0) v = __ldg(d.site_vox + n);
     wait_prior_grid();
     allow_next_grid();
-    if (n < 0) return;
-    int a, b;
-    unpack_sums(d.acc[PAR][n], a, b);
-    float Nt, phi;
-    sums_phase(a, b, Nt, phi);
-    if (dst < 0) {
-        d.phi[PAR][v] = phi;
-        if constexpr (WRITE_N) d.nsum[n] = Nt;
-    } else {
-        d.phi[PAR][dst] = phi;    // halo voxel of a periodic face
+    unsigned long long s[PER];
+    #pragma unroll
+    for (int k = 0; k < PER; ++k) s[k] = n[k] >= 0 ? ld_keep(d.acc[PAR] + n[k], pol) : 0ull;
+    #pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        if (n[k] < 0) continue;
+        int a, b;
+        unpack_sums(s[k], a, b);
+        float Nt, phi;
+        sums_phase(a, b, Nt, phi);
+        if (dst[k] < 0) {
+            d.phi[PAR][v[k]] = phi;
+            if constexpr (WRITE_N) d.nsum[n[k]] = Nt;
+            st_keep(d.acc[PAR ^ 1] + n[k], 0ull, pol);
+        } else {
+            d.phi[PAR][dst[k]] = phi;    // halo voxel of a periodic face
+        }
     }
 }
 
@@ -611,6 +652,7 @@ __device__ __forceinline__ void collide_site(const DomainView& d, int n, const f
             rb = __float2int_rn(NbK * kFix);
         }
         unsigned long long* const acc = d.acc[PAR ^ 1];
+        const unsigned long long pol = l2_keep();
         static_for<1, Q7>([&](auto qc) {
             constexpr int q = decltype(qc)::value;
             float ux = 0.0f, nn = 0.0f;
@@ -631,14 +673,13 @@ __device__ __forceinline__ void collide_site(const DomainView& d, int n, const f
                 m = static_cast<unsigned>(sl) < static_cast<unsigned>(d.n_sites) ? sl : -1;
             }
             if (m >= 0) {
-                red_add(acc + m, pack_sums(ia, ib));
+                red_add(acc + m, pack_sums(ia, ib), pol);
             } else {
                 ra += ia;
                 rb += ib;
             }
         });
-        red_add(acc + n, pack_sums(ra, rb));
-        d.acc[PAR][n] = 0ull;    // this step's sums are consumed: they receive the step after next
+        red_add(acc + n, pack_sums(ra, rb), pol);
         return;
     }
     T* const A = static_cast<T*>(d.a);
@@ -692,7 +733,7 @@ __device__ __forceinline__ void collide_site(const DomainView& d, int n, const f
 // One site per thread, direct loads.
 template <int PAR, class S, int CF = 0>
 __device__ __forceinline__ void collide_thread(const DomainView& d, int n, SlotCache sc) {
-    const int v = __ldg(d.site_vox + n);
+    const int v = CF != 0 ? ldg_keep(d.site_vox + n, l2_keep()) : __ldg(d.site_vox + n);
     float f[Q19];
     load_f<PAR, S>(d, n, v, f, sc);
     if constexpr (CF != 0 && PAR == 0) {
@@ -705,7 +746,7 @@ __device__ __forceinline__ void collide_thread(const DomainView& d, int n, SlotC
     // sum form from the sums: the site's own Na, Nb (complete before the
     // previous phase pass, like f)
     int a_own = 0, b_own = 0;
-    if constexpr (CF == 2) unpack_sums(d.acc[PAR][n], a_own, b_own);
+    if constexpr (CF == 2) unpack_sums(ld_keep(d.acc[PAR] + n, l2_keep()), a_own, b_own);
 
     // Everything above (site and neighbour ids, f and the sums from the
     // previous collision) is safe to read before the phase pass of this step
