@@ -137,7 +137,7 @@ __global__ void __launch_bounds__(BT) k_batch_measure(const DomainView* views, c
             reinterpret_cast<int*>(&sv)[threadIdx.x] = reinterpret_cast<const int*>(views + tl.job)[threadIdx.x];
         if (threadIdx.x == 0) par = parity[tl.job];
         __syncthreads();
-        Acc2 acc[NSUM];
+        AccF64 acc[NSUM];
         const int n = tl.first + threadIdx.x;
         if (n < sv.n_sites) {
             if (par) measure_site<1, S>(sv, n, acc);

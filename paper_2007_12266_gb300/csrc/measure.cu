@@ -21,7 +21,7 @@ inline unsigned blocks_for(long long n) { return static_cast<unsigned>((n + kBlo
 
 template <int PAR, class S>
 __global__ void __launch_bounds__(kBlock) k_measure(DomainView d, double* partials) {
-    Acc2 acc[NSUM];
+    AccF64 acc[NSUM];
     for (int n = blockIdx.x * kBlock + threadIdx.x; n < d.n_sites; n += gridDim.x * kBlock)
         measure_site<PAR, S>(d, n, acc);
     block_reduce_sums<kBlock>(acc, partials + static_cast<size_t>(blockIdx.x) * NSUM);

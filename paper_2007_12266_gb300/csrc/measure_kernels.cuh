@@ -28,19 +28,13 @@ __device__ __forceinline__ void load_site(const DomainView& d, int n, float (&f)
     load_components<PAR, S>(d, n, v, nb, a, b);
 }
 
-// Compensated fp32 accumulator (TwoSum): hi + lo carries about 48 bits, so a
-// thread's few dozen sites sum as accurately as in fp64 while using the fp32
-// pipes; block and global reductions are fp64.
-struct Acc2 {
-    float hi = 0.0f, lo = 0.0f;
-    __device__ __forceinline__ void add(float x) {
-        const float s = hi + x;
-        const float bp = s - hi;
-        const float err = (hi - (s - bp)) + (x - bp);
-        hi = s;
-        lo += err;
-    }
-    __device__ __forceinline__ double value() const { return static_cast<double>(hi) + static_cast<double>(lo); }
+// fp64 accumulator of per-site fp32 quantities: every sum of the basic
+// analysis is formed in fp64, from each thread's sites through the block and
+// global reductions.
+struct AccF64 {
+    double s = 0.0;
+    __device__ __forceinline__ void add(float x) { s += static_cast<double>(x); }
+    __device__ __forceinline__ double value() const { return s; }
 };
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -57,7 +51,7 @@ __device__ __forceinline__ double warp_sum(double v) {
 //  or a non-positive total density (small negative densities are legitimate
 //  next to interfaces and are not counted)
 template <int PAR, class S>
-__device__ __forceinline__ void measure_site(const DomainView& d, int n, Acc2 (&acc)[NSUM]) {
+__device__ __forceinline__ void measure_site(const DomainView& d, int n, AccF64 (&acc)[NSUM]) {
     const float hfx = 0.5f * d.fx, hfy = 0.5f * d.fy, hfz = 0.5f * d.fz;
     float f[Q19], a[Q7], b[Q7];
     load_site<PAR, S>(d, n, f, a, b);
@@ -117,7 +111,7 @@ __device__ __forceinline__ void measure_site(const DomainView& d, int n, Acc2 (&
 
 // Block-wide fp64 reduction of the accumulators into out[0..NSUM) (thread 0..NSUM-1 write).
 template <int BT>
-__device__ __forceinline__ void block_reduce_sums(Acc2 (&acc)[NSUM], double* out) {
+__device__ __forceinline__ void block_reduce_sums(AccF64 (&acc)[NSUM], double* out) {
     __shared__ double red[BT / 32][NSUM];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll

@@ -169,14 +169,15 @@ __device__ __forceinline__ void unpack_sums(unsigned long long s, int& a, int& b
     b = static_cast<int>(static_cast<unsigned>(s));
     a = static_cast<int>((static_cast<long long>(s) - static_cast<long long>(b)) >> 32);
 }
-// N = Na + Nb and phi = (Na - Nb)/(Na + Nb) of a site from its sums; the phase
-// pass and the collision both use this function, so they agree bit for bit.
+// N = Na + Nb and phi = (Na - Nb)/(Na + Nb) of a site from its sums, in fp32
+// (32-bit integer to float conversions: a 64-bit conversion runs on the fp64
+// pipe, which is slow on this GPU); the phase pass and the collision both use
+// this function, so they agree bit for bit.
 __device__ __forceinline__ void sums_phase(int a, int b, float& Nt, float& phi) {
-    const long long nt = static_cast<long long>(a) + b;
-    const long long dd = static_cast<long long>(a) - b;
-    const float ntf = static_cast<float>(nt);
-    Nt = ntf * kSumInv;
-    phi = nt > 0 ? static_cast<float>(dd) / ntf : 0.0f;
+    const float fa = static_cast<float>(a), fb = static_cast<float>(b);
+    const float nt = fa + fb;
+    Nt = nt * kSumInv;
+    phi = nt > 0.0f ? (fa - fb) / nt : 0.0f;
 }
 // The sums and the site -> voxel map (8 + 4 bytes per site, read by the phase
 // pass and again by the collision) are accessed with an L2 evict-last policy,

@@ -77,6 +77,57 @@ def test_batch_matches_alone(precision):
     b.close()
 
 
+@pytest.mark.parametrize("precision", ["fp32", "fp16"])
+def test_batched_jobs_match_the_oracle(precision):
+    """Every job of the uneven set (three periodicities, two viscosity pairs,
+    a reservoir job) advanced in one batch against its own FP64 oracle: one
+    even plus one odd step per distribution (FP32: 2 x 1e-6 max(|o|, w_q),
+    one-step bound per step; FP16: from what its store holds, twice the
+    storage bounds of the FP16 one-step test), then saturation and Darcy flux
+    after 200 steps within 1e-3."""
+    import oracle
+    import paper_2007_12266_gb300 as lbm
+    specs = _jobs()
+    doms = [_make(s, precision) for s in specs]
+    refs = []
+    for (lab, aff, phi0, per, kw), d in zip(specs, doms):
+        o = oracle.Oracle(lab, aff, per, **kw)
+        if precision == "fp32":
+            o.init_fluids(phi0)
+        else:
+            o.set_state(*[d.distributions(k).astype(np.float64) for k in ("f", "a", "b")], step=0)
+        refs.append(o)
+    b = lbm.Batch()
+    for d in doms:
+        b.add(d)
+    b.advance(2)
+    for j, (d, o) in enumerate(zip(doms, refs)):
+        o.step(2)
+        f, A, B = o.state()
+        if precision == "fp32":
+            for which, ref, floor in (("f", f, T19), ("a", A, W7), ("b", B, W7)):
+                g = d.distributions(which).astype(np.float64)
+                err = np.abs(g - ref) / np.maximum(np.abs(ref), floor[:, None])
+                assert err.max() <= 2e-6, (j, which, err.max())
+        else:
+            ef = np.abs(d.distributions("f") - f) / T19[:, None]
+            assert ef.max() < 2 * 5e-5, (j, ef.max())
+            for which, ref in (("a", A), ("b", B)):
+                g = d.distributions(which).astype(np.float64)
+                assert (np.abs(g - ref) / np.maximum(np.abs(ref), W7[:, None])).max() < 2 * 2e-3, (j, which)
+    b.advance(198)
+    for j, (m, o) in enumerate(zip(b.measure(), refs)):
+        o.step(198)
+        mo = o.measure()
+        assert m["step"] == mo["step"] == 200
+        assert abs(m["sat_mass"] / mo["sat_mass"] - 1) <= 1e-3, (j, m["sat_mass"], mo["sat_mass"])
+        # the flux along each job's drive (z, or x for the job driven along x)
+        a = int(np.argmax(np.abs(specs[j][4]["force"]))) if j != 3 else 2
+        key = "flux_" + "xyz"[a]
+        assert abs(m["flux"][a] - mo[key]) <= 1e-3 * abs(mo[key]), (j, m["flux"][a], mo[key])
+    b.close()
+
+
 def test_batch_membership_and_tuner():
     import paper_2007_12266_gb300 as lbm
     specs = _jobs()[:3]
