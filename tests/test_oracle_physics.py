@@ -13,11 +13,18 @@
   plane (dp = sigma / R; pins m9, m11, m13, m14, m15) and a sphere
   (dp = 2 sigma / R).
 * Contact angle (Sec. 3.2, Eq. phi_s): cos(theta) = phi_s on a flat plate,
-  phi_s = +1 water-wet (fluid A, phi > 0, wets). The paper states the
-  relation as established by earlier lattice studies; this model reproduces it
-  approximately (cos(theta) ~ 1.3 phi_s at |phi_s| = 0.5), so the pin checks
-  the neutral angle, the A/B antisymmetry, the sign convention and the angle
-  within 15 degrees.
+  phi_s = +1 water-wet (fluid A, phi > 0, wets). The angle depends on the
+  strength of the alpha|C| stress terms relative to the colour segregation:
+  converged drops at phi_s = 0.5 give 58.2, 56.7, 53.0, 47.3, 41.4 degrees for
+  alpha = 0.00083, 0.00125, 0.0025, 0.005, 0.01. The paper's two statements on
+  the colour gradient (C = grad phi, and sigma = 6 alpha with the printed
+  alpha|C|/2 terms) fix that strength differently: the stencil C = 6 grad phi
+  taken here makes sigma = 6 alpha hold (the Laplace pins) and gives
+  cos(theta) ~ 1.35 phi_s at alpha = 0.005; the stress scale of C = grad phi is
+  the same model at alpha / 6, where cos(theta) = phi_s holds within 2 degrees.
+  The pins check the neutral angle, the A/B antisymmetry, the sign convention
+  and the angle within 15 degrees at the paper's alpha, and the closed form
+  cos(theta) = phi_s within 3 degrees at the stress scale of C = grad phi.
 """
 import json
 import os
@@ -184,14 +191,14 @@ def _interface_points(ph, zmin):
     return np.array(pts)
 
 
-def _contact_angle(phis, nx=96, nz=48, R0=14, steps=8000):
+def _contact_angle(phis, nx=96, nz=48, R0=14, steps=8000, alpha=0.005):
     lab = np.zeros((nz, 1, nx), np.uint16)
     lab[0] = 1
     aff = np.where(lab != 0, phis, 0).astype(np.float32)
     z, x = np.meshgrid(np.arange(nz), np.arange(nx), indexing="ij")
     d = np.sqrt((x - nx / 2) ** 2 + (z - 0.5) ** 2)
     phi0 = np.where(d < R0, 1.0, -1.0).astype(np.float32).reshape(nz, 1, nx)
-    o = oracle.Oracle(lab, aff, (1, 1, 0), tau_a=0.7, tau_b=0.7, alpha=0.005, beta=0.95)
+    o = oracle.Oracle(lab, aff, (1, 1, 0), tau_a=0.7, tau_b=0.7, alpha=alpha, beta=0.95)
     o.init_fluids(phi0)
     o.step(steps)
     phi, _, _ = o.fields()
@@ -212,3 +219,12 @@ def test_contact_angle_against_affinity():
     assert th[0.5] < th[0.0] < th[-0.5]               # phi_s = +1 water-wet (A wets)
     for ps, t in th.items():
         assert abs(t - np.degrees(np.arccos(ps))) < 15, (ps, t)
+
+
+def test_contact_angle_is_acos_phis_at_the_stress_scale_of_the_plain_gradient():
+    """cos(theta) = phi_s (Sec. 3.2) with the interfacial stress at the scale of
+    C = grad(phi): the same model with alpha / 6 (alpha enters only as
+    alpha|C|). A wetting drop (phi_s = 0.5, radius of curvature 23 voxels,
+    five interface widths) converges to 58.2 degrees; the gate is 3 degrees."""
+    th = _contact_angle(0.5, steps=32000, alpha=0.005 / 6)
+    assert abs(th - 60.0) < 3.0, th
