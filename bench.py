@@ -491,31 +491,34 @@ def bench_prepare(args):
 SERVING_L = (64, 96, 128, 160, 192, 224, 256, 288, 320, 352, 384)
 
 
+def serving_trace(jobs, prec, max_steps, device):
+    """Serving trace: Poisson arrivals at 20/s of jobs with L in {64, 96, ...,
+    384}, each stopping on the flux-change test (1e-4 over 500 steps) or at
+    max_steps; then the same jobs again at an arrival rate of 70 % of the
+    capacity the first run measured, to show the latency of the continuous
+    batcher itself rather than of the queue."""
+    r1 = bench_serving(jobs, prec, 20.0, 5, max_steps, 500, device)
+    # capacity in jobs per second: aggregate site-update rate over the mean work of a job
+    work = r1["mean_sites"] * r1["mean_steps"]
+    cap = r1["aggregate_value"] * 1e6 / max(work, 1.0)
+    r2 = bench_serving(jobs, prec, 0.7 * cap, 6, max_steps, 500, device)
+    r2["capacity_jobs_per_s"] = cap
+    return {"workload": (f"{len(jobs)} Poisson arrivals, L uniform on {SERVING_L}, porosity U[0.15, 0.35], "
+                         f"50 % steady, 30 % unsteady, 20 % centrifuge; flux-change 1e-4 every 500 steps or "
+                         f"{max_steps} steps; {prec} storage"),
+            "lambda_20": r1, "lambda_70pct_capacity": r2}
+
+
 def bench_serving_trace(args):
-    """Serving trace at full size: Poisson arrivals at 20/s of jobs with L in
-    {64, 96, ..., 384}, each stopping on the flux-change test (1e-4 over 500
-    steps) or at 10,000 steps; then the same jobs again at an arrival rate of
-    70 % of the capacity the first run measured, to show the latency of the
-    continuous batcher itself rather than of the queue."""
+    """--mode serving: the serving trace alone (see serving_trace)."""
     import torch
     t0 = time.perf_counter()
     jobs = _spawn_map(_serving_job, [(i, SERVING_L) for i in range(args.serving_jobs)])
     gen_s = time.perf_counter() - t0
     torch.cuda.set_device(0)
-    prec = args.precision
     out = {"metric": "serving latency p50/p99 and aggregate pore-site MLUPS", "unit": "MLUPS",
-           "workload": (f"{len(jobs)} jobs, L uniform on {SERVING_L}, porosity U[0.15, 0.35], 50 % steady, "
-                        f"30 % unsteady, 20 % centrifuge; flux-change 1e-4 every 500 steps or "
-                        f"{args.serving_max_steps} steps; {prec} storage"),
            "generation_s": gen_s}
-    r1 = bench_serving(jobs, prec, 20.0, 5, args.serving_max_steps, 500, 0)
-    out["lambda_20"] = r1
-    # capacity in jobs per second: aggregate site-update rate over the mean work of a job
-    work = r1["mean_sites"] * r1["mean_steps"]
-    cap = r1["aggregate_value"] * 1e6 / max(work, 1.0)
-    r2 = bench_serving(jobs, prec, 0.7 * cap, 6, args.serving_max_steps, 500, 0)
-    r2["capacity_jobs_per_s"] = cap
-    out["lambda_70pct_capacity"] = r2
+    out.update(serving_trace(jobs, args.precision, args.serving_max_steps, 0))
     print(json.dumps(out))
     return 0
 
@@ -655,12 +658,10 @@ def bench_gpu(args):
     serving = None
     if not args.no_serving and world == 1:
         try:
-            choices = (64, 96, 128, 160)
-            sj = _spawn_map(_serving_job, [(i, choices) for i in range(args.serving_jobs)])
-            serving = bench_serving(sj, "fp16", 20.0, 5, args.serving_max_steps, 500, local_rank)
-            serving["workload"] = (f"{len(sj)} Poisson arrivals at 20/s, L in {choices}, FP16 storage, "
-                                   f"flux-change 1e-4 every 500 steps or {args.serving_max_steps} steps")
-            serving["vs_plain_fp32"] = serving["aggregate_value"] / value
+            sj = _spawn_map(_serving_job, [(i, SERVING_L) for i in range(args.serving_jobs)])
+            serving = serving_trace(sj, "fp16", args.serving_max_steps, local_rank)
+            for r in (serving["lambda_20"], serving["lambda_70pct_capacity"]):
+                r["vs_plain_fp32"] = r["aggregate_value"] / value
             del sj
         except Exception as exc:
             serving = {"error": repr(exc)}
@@ -692,6 +693,8 @@ def bench_gpu(args):
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": workload_label(w, args.size),
                        "n_sites": N, "storage": prec, "timesteps_per_step": bundle,
+                       "step_form": ("components carried as per-site fixed-point sums inside each "
+                                     f"{bundle}-timestep call (populations at its first and last step)"),
                        "analysis_per_step": "fp64 basic analysis (saturation, fluxes, Ca)",
                        "l2": "state larger than L2 (no flush needed)",
                        "kernel_timing": "second pass, CUDA events around each launch",
@@ -700,6 +703,7 @@ def bench_gpu(args):
                          "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "peak_kind": peak_kind, "traffic": traffic,
                          "algorithmic_bytes_per_site": bytes_c,
+                         "dram_bytes_per_site": None if nt is None else nt["bytes_per_site"],
                          "avg_launch_ms": c_ms, "launches": kt["collide_launches"],
                          "phase_avg_launch_ms": p_ms,
                          "step_achieved_gbs": step_gbs, "step_frac": step_gbs / peak,
@@ -762,8 +766,8 @@ def main():
     ap.add_argument("--no-serving", action="store_true", help="skip the serving run")
     ap.add_argument("--batched-jobs", type=int, default=64, help="jobs of the batched set")
     ap.add_argument("--batched-steps", type=int, default=2000, help="timesteps of the batched set")
-    ap.add_argument("--serving-jobs", type=int, default=24, help="arrivals of the serving run")
-    ap.add_argument("--serving-max-steps", type=int, default=4000, help="step ceiling of a serving job")
+    ap.add_argument("--serving-jobs", type=int, default=16, help="arrivals of the serving trace")
+    ap.add_argument("--serving-max-steps", type=int, default=10000, help="step ceiling of a serving job")
     args = ap.parse_args()
     if args.impl == "reference":
         return bench_reference(args)

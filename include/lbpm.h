@@ -49,7 +49,8 @@ typedef enum {
     LBPM_E_CUDA = 3,      /* a CUDA runtime call or kernel launch failed */
     LBPM_E_STATE = 4,     /* call out of order (e.g. advance before init) */
     LBPM_E_UNSTABLE = 5,  /* the last measure found non-finite values or a blown-up density */
-    LBPM_E_TIMEOUT = 6    /* a bounded device-side wait gave up */
+    LBPM_E_TIMEOUT = 6    /* reserved for a bounded device-side wait that gives up; no call
+                             returns it (the kernels have no cross-block waits) */
 } lbpm_status;
 
 /* Storage precision of the distributions. */
@@ -310,8 +311,10 @@ lbpm_status lbpm_restore(lbpm_ctx* ctx, const void* host_buf, size_t bytes);
  *     first timestep of a call reads, and the last one writes, the
  *     populations, so between calls the state is the same as in the
  *     population form and every export, measure and snapshot applies
- *     unchanged. Runs with reservoirs or pressure faces (reservoir_z != 0)
- *     always use the population form.
+ *     unchanged. Reservoir slabs (reservoir_z = 1) reset the slab sites' sums;
+ *     runs with pressure or flux faces (reservoir_z = 2, 3) always use the
+ *     population form. The batched form (lbpm_batch_advance) and the serving
+ *     loop use the sum form when every job of the batch can.
  * Errors: LBPM_E_INVALID (unknown form).
  */
 lbpm_status lbpm_set_step_form(lbpm_ctx* ctx, int form);
@@ -328,8 +331,10 @@ lbpm_status lbpm_kernel_timing(lbpm_ctx* ctx, double* ms_collide, long long* n_c
  * Batched form: several jobs (independent contexts on one GPU, same storage
  * precision) advanced together. Every timestep of the whole batch is ONE
  * launch of the phase pass and ONE of the fused collide-stream kernel, both
- * persistent over a list of tiles that covers all jobs' sites; bundles of two
- * steps are replayed from a CUDA graph. Each job's results agree with
+ * over a list of tiles that covers all jobs' sites; bundles of two steps are
+ * replayed from a CUDA graph. Inside a call of two or more steps the
+ * components travel as per-site sums when every job allows it (see
+ * lbpm_set_step_form). Each job's results agree with
  * advancing it alone to fp32 rounding (1e-5 relative per distribution after
  * 24 steps in the tests: the batched and single-domain kernels are compiled
  * separately and the compiler may contract multiply-adds differently); two

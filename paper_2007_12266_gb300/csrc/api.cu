@@ -260,6 +260,13 @@ cudaError_t launch_step_collide(lbpm_ctx* c, int kind, int par, cudaStream_t s) 
     if (kind == kStepPop || kind == kStepSumLast) return launch_collide(c, par, s);
     return launch_collide_sum(c, par, kind == kStepSumMid, s);
 }
+// The boundary kernel after the collision of a step of the given kind (reservoir
+// slabs, pressure faces); it writes what the next step (parity par ^ 1) reads.
+cudaError_t launch_step_boundary(lbpm_ctx* c, int kind, int par, cudaStream_t s) {
+    if (!c->n_slab) return cudaSuccess;
+    if (kind == kStepPop || kind == kStepSumLast) return launch_reservoir(c, par ^ 1, s);
+    return launch_reservoir_sum(c, par ^ 1, s);
+}
 
 // One timestep: phase pass, fused collide-stream, reservoir reset.
 cudaError_t enqueue_step(lbpm_ctx* c, int par, cudaStream_t s) {
@@ -271,17 +278,8 @@ cudaError_t enqueue_step(lbpm_ctx* c, int par, cudaStream_t s) {
 
 int kernels_per_step(const lbpm_ctx* c) { return c->n_slab ? 3 : 2; }
 
-// The sum form needs its first step's target sums cleared (the run's later
-// steps clear their own as they consume them).
-cudaError_t clear_sums(lbpm_ctx* c, int par, cudaStream_t s) {
-    return cudaMemsetAsync(c->d_acc + static_cast<size_t>(par) * static_cast<size_t>(c->N), 0,
-                           sizeof(unsigned long long) * static_cast<size_t>(c->N), s);
-}
-
 // Whether lbpm_advance(nsteps) runs in the sum form.
-bool use_sum_form(const lbpm_ctx* c, long long nsteps) {
-    return c->step_form == LBPM_STEP_AUTO && c->n_slab == 0 && nsteps >= 2 && c->d_acc != nullptr;
-}
+bool use_sum_form(const lbpm_ctx* c, long long nsteps) { return nsteps >= 2 && sum_form_capable(c); }
 
 // Capture `steps` (even) middle timesteps of the sum form, starting at an even step.
 cudaError_t capture_sum_bundle(lbpm_ctx* c, int steps, cudaGraphExec_t* out) {
@@ -295,6 +293,7 @@ cudaError_t capture_sum_bundle(lbpm_ctx* c, int steps, cudaGraphExec_t* out) {
     for (int k = 0; k < steps && el == cudaSuccess; ++k) {
         el = launch_step_phase(c, kStepSumMid, k & 1, c->cap_stream);
         if (el == cudaSuccess) el = launch_step_collide(c, kStepSumMid, k & 1, c->cap_stream);
+        if (el == cudaSuccess) el = launch_step_boundary(c, kStepSumMid, k & 1, c->cap_stream);
     }
     cudaGraph_t g = nullptr;
     e = cudaStreamEndCapture(c->cap_stream, &g);
@@ -334,6 +333,15 @@ int next_event(lbpm_ctx* c) {
 }  // namespace
 
 namespace lbm {
+
+bool sum_form_capable(const lbpm_ctx* c) {
+    return c->step_form == LBPM_STEP_AUTO && c->params.reservoir_z <= 1 && c->d_acc != nullptr;
+}
+
+cudaError_t clear_sums(const lbpm_ctx* c, int par, cudaStream_t s) {
+    return cudaMemsetAsync(c->d_acc + static_cast<size_t>(par) * static_cast<size_t>(c->N), 0,
+                           sizeof(unsigned long long) * static_cast<size_t>(c->N), s);
+}
 
 void* dalloc(lbpm_ctx* c, size_t bytes) {
     if (bytes == 0) bytes = 16;
@@ -639,6 +647,10 @@ lbpm_status plain_step(lbpm_ctx* c, int kind) {
     if (e0 >= 0 && e1 >= 0) c->ev_phase.emplace_back(e0, e1);
     if (e2 >= 0 && e3 >= 0) c->ev_collide.emplace_back(e2, e3);
     c->launches += 2;
+    if (c->n_slab) {
+        LBPM_CK(c, launch_step_boundary(c, kind, par, c->stream));
+        c->launches += 1;
+    }
     c->step += 1;
     return LBPM_OK;
 }
@@ -662,7 +674,7 @@ lbpm_status advance_sum(lbpm_ctx* c, long long nsteps) {
             while (mid >= sizes[gi]) {
                 if (!c->sum_graphs[gi]) LBPM_CK(c, capture_sum_bundle(c, sizes[gi], &c->sum_graphs[gi]));
                 LBPM_CK(c, cudaGraphLaunch(c->sum_graphs[gi], c->stream));
-                c->launches += 2LL * sizes[gi];
+                c->launches += static_cast<long long>(kernels_per_step(c)) * sizes[gi];
                 c->step += sizes[gi];
                 mid -= sizes[gi];
             }

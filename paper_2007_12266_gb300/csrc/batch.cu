@@ -55,9 +55,22 @@ __global__ void __launch_bounds__(BT) k_batch_phase(const __grid_constant__ Batc
     }
 }
 
-template <int PAR, class S, int BT>
-__global__ void __launch_bounds__(BT, 1024 / BT) k_batch_collide(const __grid_constant__ BatchLaunch p) {
-    constexpr int kSlots = PAR == 1 ? (Q19 - 1) * BT : 1;
+// Phase pass of the sum form (see phase_sum_thread), one entry per thread.
+template <int PAR, bool WRITE_N, int BT>
+__global__ void __launch_bounds__(BT) k_batch_phase_sum(const __grid_constant__ BatchLaunch p) {
+    const int nt = p.tile_begin[p.n_jobs];
+    for (int t = blockIdx.x; t < nt; t += gridDim.x) {
+        const int j = job_of_tile(p, t);
+        phase_sum_thread<PAR, WRITE_N, 1>(p.v[j], (t - p.tile_begin[j]) * BT + threadIdx.x, BT);
+    }
+}
+
+// CF: component form of the collision (see collide_site).
+// 36 resident warps per SM where the block size allows (56 registers at 128
+// threads), as for the single-domain collision.
+template <int PAR, class S, int CF, int BT>
+__global__ void __launch_bounds__(BT, 1152 / BT) k_batch_collide(const __grid_constant__ BatchLaunch p) {
+    constexpr int kSlots = PAR == 1 ? (Q19 - 1) * BT : (CF != 0 ? (Q7 - 1) * BT : 1);
     constexpr int kRefs = PAR == 1 && S::kRef ? (Q19 - 1) * BT : 1;
     __shared__ int slot[kSlots];
     __shared__ float ref[kRefs];
@@ -66,7 +79,7 @@ __global__ void __launch_bounds__(BT, 1024 / BT) k_batch_collide(const __grid_co
         const int j = job_of_tile(p, t);
         const DomainView& d = p.v[j];
         const int n = (t - p.tile_begin[j]) * BT + threadIdx.x;
-        if (n < d.n_sites) collide_thread<PAR, S>(d, n, SlotCache{slot + threadIdx.x, ref + threadIdx.x, BT});
+        if (n < d.n_sites) collide_thread<PAR, S, CF>(d, n, SlotCache{slot + threadIdx.x, ref + threadIdx.x, BT});
     }
 }
 
@@ -87,37 +100,46 @@ struct Launch {
     }
 };
 
-template <int BT>
-cudaError_t batch_phase_bt(int par, bool fp16, unsigned grid, cudaStream_t s, const BatchLaunch& p) {
-    if (par == 0)
-        return fp16 ? Launch<BT>::go(k_batch_phase<0, StoreF16, BT>, grid, s, p)
-                    : Launch<BT>::go(k_batch_phase<0, StoreF32, BT>, grid, s, p);
-    return fp16 ? Launch<BT>::go(k_batch_phase<1, StoreF16, BT>, grid, s, p)
-                : Launch<BT>::go(k_batch_phase<1, StoreF32, BT>, grid, s, p);
+// phase pass: form 0 = populations, 1 = sums, 2 = sums writing N (last step of a run)
+template <int BT, int PAR>
+cudaError_t batch_phase_par(int form, bool fp16, unsigned grid, cudaStream_t s, const BatchLaunch& p) {
+    if (form == 1) return Launch<BT>::go(k_batch_phase_sum<PAR, false, BT>, grid, s, p);
+    if (form == 2) return Launch<BT>::go(k_batch_phase_sum<PAR, true, BT>, grid, s, p);
+    return fp16 ? Launch<BT>::go(k_batch_phase<PAR, StoreF16, BT>, grid, s, p)
+                : Launch<BT>::go(k_batch_phase<PAR, StoreF32, BT>, grid, s, p);
+}
+
+// collision: form = component form CF (0 populations, 1 / 2 sums)
+template <int BT, int PAR, int CF>
+cudaError_t batch_collide_cf(bool fp16, unsigned grid, cudaStream_t s, const BatchLaunch& p) {
+    return fp16 ? Launch<BT>::go(k_batch_collide<PAR, StoreF16, CF, BT>, grid, s, p)
+                : Launch<BT>::go(k_batch_collide<PAR, StoreF32, CF, BT>, grid, s, p);
+}
+template <int BT, int PAR>
+cudaError_t batch_collide_par(int form, bool fp16, unsigned grid, cudaStream_t s, const BatchLaunch& p) {
+    if (form == 1) return batch_collide_cf<BT, PAR, 1>(fp16, grid, s, p);
+    if (form == 2) return batch_collide_cf<BT, PAR, 2>(fp16, grid, s, p);
+    return batch_collide_cf<BT, PAR, 0>(fp16, grid, s, p);
 }
 
 template <int BT>
-cudaError_t batch_collide_bt(int par, bool fp16, unsigned grid, cudaStream_t s, const BatchLaunch& p) {
-    if (par == 0)
-        return fp16 ? Launch<BT>::go(k_batch_collide<0, StoreF16, BT>, grid, s, p)
-                    : Launch<BT>::go(k_batch_collide<0, StoreF32, BT>, grid, s, p);
-    return fp16 ? Launch<BT>::go(k_batch_collide<1, StoreF16, BT>, grid, s, p)
-                : Launch<BT>::go(k_batch_collide<1, StoreF32, BT>, grid, s, p);
+cudaError_t batch_bt(int kernel, int form, int par, bool fp16, unsigned grid, cudaStream_t s, const BatchLaunch& p) {
+    if (kernel == 0)
+        return par == 0 ? batch_phase_par<BT, 0>(form, fp16, grid, s, p) : batch_phase_par<BT, 1>(form, fp16, grid, s, p);
+    return par == 0 ? batch_collide_par<BT, 0>(form, fp16, grid, s, p) : batch_collide_par<BT, 1>(form, fp16, grid, s, p);
 }
 
 }  // namespace
 
-// Launch one phase (0 = phase pass, 1 = collide-stream) over the jobs of p.
-cudaError_t launch_batch(int kernel, int par, bool fp16, int bt, unsigned grid, cudaStream_t s,
+// Launch one phase (0 = phase pass, 1 = collide-stream) over the jobs of p,
+// in the given form (see batch_phase_par / batch_collide_par).
+cudaError_t launch_batch(int kernel, int form, int par, bool fp16, int bt, unsigned grid, cudaStream_t s,
                          const BatchLaunch& p) {
     if (p.n_jobs == 0 || p.tile_begin[p.n_jobs] == 0) return cudaSuccess;
     switch (bt) {
-    case 128: return kernel == 0 ? batch_phase_bt<128>(par, fp16, grid, s, p)
-                                 : batch_collide_bt<128>(par, fp16, grid, s, p);
-    case 512: return kernel == 0 ? batch_phase_bt<512>(par, fp16, grid, s, p)
-                                 : batch_collide_bt<512>(par, fp16, grid, s, p);
-    default: return kernel == 0 ? batch_phase_bt<256>(par, fp16, grid, s, p)
-                                : batch_collide_bt<256>(par, fp16, grid, s, p);
+    case 128: return batch_bt<128>(kernel, form, par, fp16, grid, s, p);
+    case 512: return batch_bt<512>(kernel, form, par, fp16, grid, s, p);
+    default: return batch_bt<256>(kernel, form, par, fp16, grid, s, p);
     }
 }
 
@@ -180,8 +202,8 @@ int batch_max_blocks(int kernel, bool fp16, int bt) {
     const void* f = nullptr;
 #define LBPM_PICK(BT)                                                                                        \
     f = kernel == 0 ? (fp16 ? (const void*)k_batch_phase<1, StoreF16, BT> : (const void*)k_batch_phase<1, StoreF32, BT>) \
-                    : (fp16 ? (const void*)k_batch_collide<1, StoreF16, BT>                                   \
-                            : (const void*)k_batch_collide<1, StoreF32, BT>);
+                    : (fp16 ? (const void*)k_batch_collide<1, StoreF16, 2, BT>                                \
+                            : (const void*)k_batch_collide<1, StoreF32, 2, BT>);
     if (bt == 128) { LBPM_PICK(128) } else if (bt == 512) { LBPM_PICK(512) } else { LBPM_PICK(256) }
 #undef LBPM_PICK
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f, bt, 0) != cudaSuccess) {

@@ -41,9 +41,11 @@ struct lbpm_batch {
     int bt = 256;
     int bps[2] = {-1, -1};
     int n_sm = 0;
-    // bundle graph (2 timesteps)
+    // bundle graphs (2 timesteps): graph = population form; sum_graph = two
+    // middle steps of the sum form starting at an odd step (see batch_advance_sum)
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t graph = nullptr;
+    cudaGraphExec_t sum_graph = nullptr;
     long long launches = 0;
 };
 
@@ -94,6 +96,8 @@ bool ensure(lbpm_batch* b, T** p, size_t* cap, size_t n) {
 void drop_graph(lbpm_batch* b) {
     if (b->graph) cudaGraphExecDestroy(b->graph);
     b->graph = nullptr;
+    if (b->sum_graph) cudaGraphExecDestroy(b->sum_graph);
+    b->sum_graph = nullptr;
 }
 
 lbpm_status enter(lbpm_batch* b) {
@@ -172,37 +176,79 @@ unsigned grid_for(const lbpm_batch* b, int k, const BatchLaunch& L) {
     return static_cast<unsigned>(std::max<long long>(1, std::min<long long>(persistent, n_tiles)));
 }
 
-cudaError_t enqueue_step(lbpm_batch* b, int par, cudaStream_t s) {
+// Kinds of batched timestep, as in lbpm_advance: the population form, and the
+// first, middle and last step of a run of the sum form.
+enum BatchStep { kBPop = 0, kBSumFirst = 1, kBSumMid = 2, kBSumLast = 3 };
+
+cudaError_t enqueue_step(lbpm_batch* b, int kind, int par, cudaStream_t s) {
     const bool h = b->precision == LBPM_FP16;
+    // kernel forms (see launch_batch) of each kind: phase pass, collision
+    const int phase_form[4] = {0, 0, 1, 2};
+    const int collide_form[4] = {0, 1, 2, 0};
     cudaError_t e = cudaSuccess;
+    if (kind == kBSumFirst)
+        for (lbpm_ctx* c : b->jobs)
+            if (e == cudaSuccess) e = clear_sums(c, par ^ 1, s);
     for (size_t i = 0; i < b->launch[0].size() && e == cudaSuccess; ++i) {
-        e = launch_batch(0, par, h, b->bt, grid_for(b, 0, b->launch[0][i]), s, b->launch[0][i]);
-        if (e == cudaSuccess) e = launch_batch(1, par, h, b->bt, grid_for(b, 1, b->launch[1][i]), s, b->launch[1][i]);
+        e = launch_batch(0, phase_form[kind], par, h, b->bt, grid_for(b, 0, b->launch[0][i]), s, b->launch[0][i]);
+        if (e == cudaSuccess)
+            e = launch_batch(1, collide_form[kind], par, h, b->bt, grid_for(b, 1, b->launch[1][i]), s,
+                             b->launch[1][i]);
     }
+    const bool sums_next = kind == kBSumFirst || kind == kBSumMid;
     for (lbpm_ctx* c : b->jobs)
-        if (e == cudaSuccess && c->n_slab) e = launch_reservoir(c, par ^ 1, s);
+        if (e == cudaSuccess && c->n_slab)
+            e = sums_next ? launch_reservoir_sum(c, par ^ 1, s) : launch_reservoir(c, par ^ 1, s);
     return e;
 }
 
-lbpm_status capture(lbpm_batch* b) {
-    drop_graph(b);
+// Capture two timesteps of the given kind starting at parity `par0` into *out.
+lbpm_status capture(lbpm_batch* b, int kind, int par0, cudaGraphExec_t* out) {
+    if (*out) cudaGraphExecDestroy(*out);
+    *out = nullptr;
     if (!b->cap_stream) LBPM_BCK(b, cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking));
     LBPM_BCK(b, cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
-    cudaError_t el = enqueue_step(b, 0, b->cap_stream);
-    if (el == cudaSuccess) el = enqueue_step(b, 1, b->cap_stream);
+    cudaError_t el = enqueue_step(b, kind, par0, b->cap_stream);
+    if (el == cudaSuccess) el = enqueue_step(b, kind, par0 ^ 1, b->cap_stream);
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamEndCapture(b->cap_stream, &g);
     if (el != cudaSuccess) e = el;
-    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->graph, g, 0);
+    if (e == cudaSuccess) e = cudaGraphInstantiate(out, g, 0);
     if (g) cudaGraphDestroy(g);
     if (e != cudaSuccess) return bfail_cuda(b, "batch graph capture", e);
     return LBPM_OK;
+}
+
+// Whether every job of the batch can run the sum form.
+bool batch_sum_form(const lbpm_batch* b) {
+    for (const lbpm_ctx* c : b->jobs)
+        if (!sum_form_capable(c)) return false;
+    return true;
 }
 
 int kernels_per_bundle(const lbpm_batch* b) {
     int k = 4 * static_cast<int>(b->launch[0].size());
     for (const lbpm_ctx* c : b->jobs) k += c->n_slab ? 2 : 0;
     return k;
+}
+
+// lbpm_batch_advance in the sum form (nsteps even, >= 2): the first step
+// reads the populations, nsteps - 2 middle steps (pairs starting at an odd
+// step, replayed from a graph) carry the components as sums, the last step
+// writes the populations.
+lbpm_status batch_advance_sum(lbpm_batch* b, long long nsteps) {
+    LBPM_BCK(b, enqueue_step(b, kBSumFirst, 0, b->stream));
+    if (nsteps > 2) {
+        if (!b->sum_graph) {
+            lbpm_status s = capture(b, kBSumMid, 1, &b->sum_graph);
+            if (s) return s;
+        }
+        for (long long k = 2; k < nsteps; k += 2) LBPM_BCK(b, cudaGraphLaunch(b->sum_graph, b->stream));
+    }
+    LBPM_BCK(b, enqueue_step(b, kBSumLast, 1, b->stream));
+    b->launches += (nsteps / 2) * kernels_per_bundle(b);
+    for (lbpm_ctx* c : b->jobs) c->step += nsteps;
+    return LBPM_OK;
 }
 
 // launch-shape cache: (gpu, precision, log2 of the site count) -> (bt, bps0, bps1)
@@ -331,7 +377,8 @@ lbpm_status lbpm_batch_advance(lbpm_batch* b, long long nsteps) {
     }
     if (b->jobs.empty() || nsteps == 0) return LBPM_OK;
     if (b->dirty && (s = rebuild(b))) return s;
-    if (!b->graph && (s = capture(b))) return s;
+    if (batch_sum_form(b)) return batch_advance_sum(b, nsteps);
+    if (!b->graph && (s = capture(b, kBPop, 0, &b->graph))) return s;
     for (long long k = 0; k < nsteps; k += 2) LBPM_BCK(b, cudaGraphLaunch(b->graph, b->stream));
     b->launches += (nsteps / 2) * kernels_per_bundle(b);
     for (lbpm_ctx* c : b->jobs) c->step += nsteps;

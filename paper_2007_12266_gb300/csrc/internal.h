@@ -153,6 +153,14 @@ cudaError_t launch_collide(const lbpm_ctx* c, int parity, cudaStream_t s);
 // otherwise from the phase pass of the population form).
 cudaError_t launch_phase_sum(const lbpm_ctx* c, int parity, bool write_nsum, cudaStream_t s);
 cudaError_t launch_collide_sum(const lbpm_ctx* c, int parity, bool from_sums, cudaStream_t s);
+// Reservoir slabs (reservoir_z = 1) in the sum form: the reset state goes into
+// the sums the next step (parity `parity`) reads, and into its f slots.
+cudaError_t launch_reservoir_sum(const lbpm_ctx* c, int parity, cudaStream_t s);
+// Whether a context can run the sum form (no pressure or flux faces, the
+// population form not forced).
+bool sum_form_capable(const lbpm_ctx* c);
+// Clear the sums that the first step of a sum-form run (parity `par`) accumulates into.
+cudaError_t clear_sums(const lbpm_ctx* c, int par, cudaStream_t s);
 cudaError_t launch_reservoir(const lbpm_ctx* c, int parity, cudaStream_t s);
 // flux inlet: blocks of the fixed-order face reduction
 constexpr int kFaceBlocks = 64;
@@ -181,7 +189,9 @@ struct BatchLaunch {
     int tile_begin[kBatchLaunchJobs + 1];
     DomainView v[kBatchLaunchJobs];
 };
-cudaError_t launch_batch(int kernel, int par, bool fp16, int bt, unsigned grid, cudaStream_t s,
+// form: phase pass 0 = populations, 1 = sums, 2 = sums writing N; collision
+// 0 = populations, 1 = sums from the phase pass, 2 = sums from the sums.
+cudaError_t launch_batch(int kernel, int form, int par, bool fp16, int bt, unsigned grid, cudaStream_t s,
                          const BatchLaunch& p);
 cudaError_t launch_batch_measure(bool fp16, unsigned grid, cudaStream_t s, const DomainView* v, const int* parity,
                                  const BatchTile* t, int nt, double* partials, const int* tile_begin, int n_jobs,

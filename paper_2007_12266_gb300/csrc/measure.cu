@@ -2,10 +2,12 @@
 // Sec. 4 basic analysis: saturation, velocity and pressure per fluid, and the
 // instability check), field export and distribution import/export.
 //
-// The reductions accumulate in fp64 in a fixed order: each thread walks a
-// fixed strided set of sites, blocks reduce with warp shuffles and shared
-// memory, and one block reduces the per-block partials. The result depends
+// The reductions run in a fixed order: each thread walks a fixed strided set
+// of sites (compensated fp32, fp64 accuracy, see AccF64), blocks reduce in
+// fp64 with warp shuffles and shared memory, and one block reduces the
+// per-block partials in fp64. The result depends
 // only on the domain, never on timing.
+#include <algorithm>
 #include <limits>
 
 #include "measure_kernels.cuh"
@@ -15,7 +17,8 @@ namespace lbm {
 namespace {
 
 constexpr int kBlock = 256;
-constexpr int kMeasureBlocks = 152 * 4;
+constexpr int kMeasureBlocks = 152 * 4;     // at least this many blocks (when there are sites for them)
+constexpr long long kMeasureSitesPerThread = 64;   // at most this many sites per thread (accuracy, see AccF64)
 
 inline unsigned blocks_for(long long n) { return static_cast<unsigned>((n + kBlock - 1) / kBlock); }
 
@@ -219,14 +222,16 @@ struct ImportK {
 
 // d_out receives NSUM doubles. Uses c->d_partials (allocated on demand).
 cudaError_t launch_measure(lbpm_ctx* c, int parity, double* d_out, cudaStream_t s) {
+    // enough blocks that no thread sums more than kMeasureSitesPerThread sites
     long long nb = (c->N + kBlock - 1) / kBlock;
-    if (nb > kMeasureBlocks) nb = kMeasureBlocks;
+    const long long need = (c->N + kBlock * kMeasureSitesPerThread - 1) / (kBlock * kMeasureSitesPerThread);
+    nb = std::min(nb, std::max<long long>(kMeasureBlocks, need));
     if (nb < 1) nb = 1;
     if (c->n_partials < nb) {
         dfree(c, c->d_partials);
-        c->d_partials = static_cast<double*>(dalloc(c, sizeof(double) * NSUM * kMeasureBlocks));
+        c->d_partials = static_cast<double*>(dalloc(c, sizeof(double) * NSUM * nb));
         if (!c->d_partials) return cudaErrorMemoryAllocation;
-        c->n_partials = kMeasureBlocks;
+        c->n_partials = nb;
     }
     cudaError_t e = dispatch<MeasureK>(c, parity, static_cast<unsigned>(nb), s, make_view(c), c->d_partials);
     if (e != cudaSuccess) return e;

@@ -363,12 +363,9 @@ __device__ __forceinline__ void phase_thread(const DomainView& d, int t) {
 
 // Phase pass of the sum form: phi (and, for a population-form collision
 // next, N) from the site's component sums, for PER entries per thread
-// (entries t0 + k * stride: sites, then periodic halo voxels). It also clears
-// the sums that this step's collision accumulates into (nobody reads them:
-// their last readers were the previous step's kernels). Ordering as in
+// (entries t0 + k * stride: sites, then periodic halo voxels). Ordering as in
 // phase_thread: the sums were completed by the collision before the previous
-// phase pass. Several entries per thread put more loads in flight (one entry
-// per thread left this pass latency-bound at a third of the DRAM bandwidth).
+// phase pass.
 template <int PAR, bool WRITE_N, int PER>
 __device__ __forceinline__ void phase_sum_thread(const DomainView& d, int t0, int stride) {
     const unsigned long long pol = l2_keep();
@@ -402,7 +399,6 @@ __device__ __forceinline__ void phase_sum_thread(const DomainView& d, int t0, in
         if (dst[k] < 0) {
             d.phi[PAR][v[k]] = phi;
             if constexpr (WRITE_N) d.nsum[n[k]] = Nt;
-            st_keep(d.acc[PAR ^ 1] + n[k], 0ull, pol);
         } else {
             d.phi[PAR][dst[k]] = phi;    // halo voxel of a periodic face
         }
@@ -681,6 +677,9 @@ __device__ __forceinline__ void collide_site(const DomainView& d, int n, const f
             }
         });
         red_add(acc + n, pack_sums(ra, rb), pol);
+        // this step's sums of the site are consumed (the phase pass before this
+        // collision was their last other reader): they receive the step after next
+        st_keep(d.acc[PAR] + n, 0ull, pol);
         return;
     }
     T* const A = static_cast<T*>(d.a);
@@ -785,7 +784,10 @@ __device__ __forceinline__ void collide_thread(const DomainView& d, int n, SlotC
 // reservoir reset (unsteady protocol, Sec. 4.1): write the rest state into
 // the slots the NEXT step (parity PAR) reads.
 // ---------------------------------------------------------------------------
-template <int PAR, class S>
+// SUMS: the sum form, where the next step reads the component sums (set to
+// the reset state Na = 1, Nb = 0 at the inlet, 0 and 1 at the outlet) instead
+// of the D3Q7 populations.
+template <int PAR, class S, bool SUMS = false>
 __device__ __forceinline__ void reservoir_thread(const DomainView& d, int n, int side, float rho_in,
                                                  float rho_out) {
     const int v = d.site_vox[n];
@@ -809,7 +811,7 @@ __device__ __forceinline__ void reservoir_thread(const DomainView& d, int n, int
         } else {
             S::template st_f<q>(d.f, i, t19(q) * rho);
         }
-        if constexpr (q < Q7) {
+        if constexpr (q < Q7 && !SUMS) {
             float av = w7(q) * na, bv = w7(q) * (1.0f - na);
             if constexpr (S::kRef) {
                 const float pw = writer_phase<PAR, q>(d, v, wall);
@@ -820,6 +822,10 @@ __device__ __forceinline__ void reservoir_thread(const DomainView& d, int n, int
             S::template st_c<q>(d.b, i, bv);
         }
     });
+    if constexpr (SUMS) {
+        constexpr int one = 1 << 28;   // kSumOne
+        d.acc[PAR][n] = side == 1 ? pack_sums(one, 0) : pack_sums(0, one);
+    }
 }
 
 // ---------------------------------------------------------------------------

@@ -143,8 +143,19 @@ def test_measures_match_oracle():
     ref.step(50)
     m, mo = dom.measure(), ref.measure()
     assert m["step"] == mo["step"] == 50 and m["n_sites"] == mo["n_sites"]
-    for k in ("sat_mass", "mass_a", "mass_b", "mass_total", "p_a", "p_b"):
-        assert abs(m[k] - mo[k]) <= 1e-5 * abs(mo[k]), k
+    # sums of the fp32 state formed to fp64 accuracy: each component is
+    # conserved exactly inside a call of the sum form and to unbiased fp32
+    # rounding by the population stores of its first and last step, so the
+    # component totals agree with the oracle's to about 1e-9 relative (measured
+    # 5e-11 on Sw, 9e-10 on the masses; gate 1e-8). The momentum populations'
+    # total Sum rho carries the fp32 rounding of every collision (measured
+    # 1.7e-8 after 50 steps; gate 1e-7), and so do the pressures of the two
+    # regions phi > 0 / phi < 0 (same gate, as long as the regions hold the
+    # same sites).
+    for k, tol in (("sat_mass", 1e-8), ("mass_a", 1e-8), ("mass_b", 1e-8), ("mass_total", 1e-7),
+                   ("p_a", 1e-7), ("p_b", 1e-7)):
+        print(k, abs(m[k] / mo[k] - 1))
+        assert abs(m[k] - mo[k]) <= tol * abs(mo[k]), k
     for k in ("sat_count", "vol_a", "vol_b"):
         assert abs(m[k] - mo[k]) <= 1e-3 * abs(mo[k]) + 2, k
     for k in ("flux", "flux_a", "flux_b", "mom_a", "mom_b"):
@@ -413,6 +424,7 @@ def test_full_size_steady256_fp16_two_steps():
         f, A, B = ref.state()
         dev = (np.abs(f - T19[:, None] * f.sum(axis=0)) / T19[:, None]).max()
         ef = np.abs(dom.distributions("f") - f) / T19[:, None]
+        print(f"fp16 full size, step {step}: max |f - o| / t_q = {ef.max():.3e}, bound {2.0 ** -10 * dev:.3e}")
         assert ef.max() < 2.0 ** -10 * dev, (step, ef.max(), dev)
         assert rel_err(dom.distributions("a"), A, W7).max() < 2e-3, step
         assert rel_err(dom.distributions("b"), B, W7).max() < 2e-3, step
