@@ -126,6 +126,9 @@ def _oracle_replay(spec, steps, interval):
 def test_served_jobs_match_the_oracle(precision):
     import paper_2007_12266_gb300 as lbm
     specs = [_job(k, j) for j, k in enumerate(["steady", "unsteady", "centrifuge"])]
+    # a plateau tolerance the injection meets within the run, so that the
+    # centrifuge rule raises the force (the replay must raise it at the same checks)
+    specs[2].update(sw_tol=3e-3, force_cap=1.6e-4)
     s = lbm.Server(max_jobs=4, check_interval=20)
     tickets = [s.submit(**sp, **POLICY, precision=precision) for sp in specs]
     for _ in range(1000):
@@ -139,6 +142,8 @@ def test_served_jobs_match_the_oracle(precision):
         mo, m = o.measure(), st["last"]
         assert mo["step"] == m["step"] == st["steps"]
         assert raises == st["force_raises"], (sp["kind"], raises, st["force_raises"])
+        if sp["kind"] == "centrifuge":
+            assert raises >= 1
         assert abs(m["sat_mass"] / mo["sat_mass"] - 1) <= 1e-3, (sp["kind"], m["sat_mass"], mo["sat_mass"])
         assert abs(m["flux"][2] - mo["flux_z"]) <= 1e-3 * abs(mo["flux_z"]), (sp["kind"], m["flux"][2], mo["flux_z"])
         print(sp["kind"], precision, st["steps"], "steps, raises", raises,
