@@ -49,8 +49,8 @@ typedef enum {
     LBPM_E_CUDA = 3,      /* a CUDA runtime call or kernel launch failed */
     LBPM_E_STATE = 4,     /* call out of order (e.g. advance before init) */
     LBPM_E_UNSTABLE = 5,  /* the last measure found non-finite values or a blown-up density */
-    LBPM_E_TIMEOUT = 6    /* reserved for a bounded device-side wait that gives up; no call
-                             returns it (the kernels have no cross-block waits) */
+    LBPM_E_TIMEOUT = 6    /* a bounded device-side wait gave up (the fused batch kernel's
+                             grid barrier; see lbpm_batch_measure, lbpm_batch_check_barrier) */
 } lbpm_status;
 
 /* Storage precision of the distributions. */
@@ -366,12 +366,20 @@ lbpm_status lbpm_batch_size(const lbpm_batch* batch, int* n_jobs, long long* n_s
 /* Advance every job by nsteps (even, asynchronous). */
 lbpm_status lbpm_batch_advance(lbpm_batch* batch, long long nsteps);
 /* Measures of every job, out[j] for the j-th job in insertion order
- * (see lbpm_measures); LBPM_E_UNSTABLE if any job is flagged. */
+ * (see lbpm_measures); LBPM_E_UNSTABLE if any job is flagged; LBPM_E_TIMEOUT
+ * if a grid barrier of the fused kernel (below) gave up waiting since the last
+ * measure (the jobs are then flagged unstable: their states are incomplete). */
 lbpm_status lbpm_batch_measure(lbpm_batch* batch, lbpm_measures* out);
 /* Launch shape: threads per block (128, 256 or 512) and resident blocks per
  * SM of the persistent phase and collide grids (0 = occupancy limit, -1 = no
- * persistent grid: one block per tile, scheduled by the hardware). A new
- * batch starts at 256 threads and -1 for both kernels. */
+ * persistent grid: one block per tile, scheduled by the hardware; -2 for both
+ * = one fused persistent kernel per bundle of steps: a cooperative grid of
+ * every block that fits the GPU runs the phase pass, the collision and the
+ * reservoir reset of all jobs, taking tiles from an atomic counter in each
+ * pass, with a grid barrier between passes whose wait gives up after 2 s; 128
+ * or 256 threads, batches of up to 112 jobs without pressure or flux faces,
+ * other batches keep the separate launches). A new batch starts at 256 threads
+ * and -1 for both kernels. */
 lbpm_status lbpm_batch_set_launch(lbpm_batch* batch, int threads, int blocks_per_sm_phase,
                                   int blocks_per_sm_collide);
 /* Autotuner: times each candidate launch shape over steps_per_candidate
@@ -383,6 +391,15 @@ lbpm_status lbpm_batch_tune(lbpm_batch* batch, int steps_per_candidate, int* thr
 /* Kernel launches the batch has issued so far (graph replays counted per
  * kernel node). Errors: LBPM_E_INVALID (NULL argument). */
 lbpm_status lbpm_batch_launch_count(const lbpm_batch* batch, long long* launches);
+/* Self-test of the fused kernel's bounded grid barrier (a library diagnostic;
+ * the paper has no counterpart): one cooperative grid of one block per SM
+ * meets at a barrier that expects `missing` more arrivals than there are
+ * blocks, with a wait limit of limit_s seconds (0 < limit_s <= 10). With
+ * missing = 0 the barrier completes (LBPM_OK); with missing > 0 nobody supplies
+ * the arrivals, every block's wait runs out after the limit and the call
+ * returns LBPM_E_TIMEOUT, with the GPU left usable. Errors: LBPM_E_INVALID,
+ * LBPM_E_OOM, LBPM_E_CUDA. */
+lbpm_status lbpm_batch_check_barrier(lbpm_batch* batch, int missing, double limit_s);
 
 /*
  * Serving loop (continuous batching) for the protocols of Sec. 4: steady

@@ -475,6 +475,16 @@ class Batch:
             self._check(st)
         return [_measures_dict(arr[j]) for j in range(len(self.jobs))]
 
+    def check_barrier(self, missing: int = 0, limit_s: float = 0.05):
+        """Self-test of the fused kernel's bounded grid barrier
+        (lbpm_batch_check_barrier): True if it completed, False if its wait ran
+        out (as it must when `missing` arrivals never come)."""
+        st = self._L.lbpm_batch_check_barrier(self._h, int(missing), float(limit_s))
+        if st == 6:
+            return False
+        self._check(st)
+        return True
+
     def set_launch(self, threads: int, blocks_per_sm_phase: int = 0, blocks_per_sm_collide: int = 0):
         self._check(self._L.lbpm_batch_set_launch(self._h, int(threads), int(blocks_per_sm_phase),
                                                   int(blocks_per_sm_collide)))

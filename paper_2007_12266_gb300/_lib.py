@@ -125,6 +125,7 @@ SIGNATURES = {
     "lbpm_batch_tune": (ct.c_int, [ct.c_void_p, ct.c_int, ct.POINTER(ct.c_int), ct.POINTER(ct.c_int),
                                    ct.POINTER(ct.c_int)]),
     "lbpm_batch_launch_count": (ct.c_int, [ct.c_void_p, ct.POINTER(ct.c_longlong)]),
+    "lbpm_batch_check_barrier": (ct.c_int, [ct.c_void_p, ct.c_int, ct.c_double]),
     "lbpm_server_create": (ct.c_int, [ct.POINTER(ct.c_void_p), ct.c_int, ct.c_void_p, ct.c_size_t, ct.c_int,
                                       ct.c_int]),
     "lbpm_server_destroy": (ct.c_int, [ct.c_void_p]),

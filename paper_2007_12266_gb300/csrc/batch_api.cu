@@ -1,6 +1,7 @@
 // C ABI of the batched form (declared in include/lbpm.h): a batch of job
 // contexts advanced together by the persistent batch kernels (batch.cu).
 #include <algorithm>
+#include <new>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -47,6 +48,14 @@ struct lbpm_batch {
     cudaGraphExec_t graph = nullptr;
     cudaGraphExec_t sum_graph = nullptr;
     long long launches = 0;
+    // fused persistent form (blocks per SM -2 for both passes, see batch_fused.cu):
+    // the job table, the barrier and tile-counter words, the error flag, and the
+    // graph of two steps (two middle steps in the sum form)
+    bool fused_ready = false;
+    FusedLaunch* fused = nullptr;
+    unsigned* d_ctl = nullptr;
+    int* d_err = nullptr;
+    cudaGraphExec_t fused_graph = nullptr;
 };
 
 namespace {
@@ -98,6 +107,8 @@ void drop_graph(lbpm_batch* b) {
     b->graph = nullptr;
     if (b->sum_graph) cudaGraphExecDestroy(b->sum_graph);
     b->sum_graph = nullptr;
+    if (b->fused_graph) cudaGraphExecDestroy(b->fused_graph);
+    b->fused_graph = nullptr;
 }
 
 lbpm_status enter(lbpm_batch* b) {
@@ -162,6 +173,35 @@ lbpm_status rebuild(lbpm_batch* b) {
     if (b->n_mtiles)
         LBPM_BCK(b, cudaMemcpyAsync(b->d_mtiles, mtiles.data(), sizeof(BatchTile) * mtiles.size(),
                                     cudaMemcpyHostToDevice, b->stream));
+    // fused table: up to kFusedJobs jobs, no pressure or flux faces
+    b->fused_ready = false;
+    bool fusable = J > 0 && J <= kFusedJobs && (b->bt == 128 || b->bt == 256);
+    for (const lbpm_ctx* c : b->jobs) fusable = fusable && c->params.reservoir_z <= 1;
+    if (fusable) {
+        if (!b->fused) b->fused = new (std::nothrow) FusedLaunch;
+        if (!b->d_ctl) b->d_ctl = static_cast<unsigned*>(balloc(b, sizeof(unsigned) * kFusedCtl));
+        if (!b->d_err) {
+            b->d_err = static_cast<int*>(balloc(b, sizeof(int)));
+            if (b->d_err) LBPM_BCK(b, cudaMemsetAsync(b->d_err, 0, sizeof(int), b->stream));
+        }
+        if (!b->fused || !b->d_ctl || !b->d_err) return bfail(b, LBPM_E_OOM, "fused batch table allocation failed");
+        FusedLaunch& F = *b->fused;
+        std::memset(&F, 0, sizeof(FusedLaunch));
+        F.n_jobs = J;
+        F.limit_ns = 2000000000ull;   // 2 s: far above any pass of a batch that fits the GPU
+        F.ctl = b->d_ctl;
+        F.err = b->d_err;
+        for (int j = 0; j < J; ++j) {
+            const lbpm_ctx* c = b->jobs[j];
+            const long long n_slab = c->params.reservoir_z == 1 ? c->n_slab : 0;
+            const long long counts[3] = {c->N + c->H, c->N, n_slab};
+            for (int k = 0; k < 3; ++k) F.tiles[k][j + 1] = F.tiles[k][j] + static_cast<int>((counts[k] + b->bt - 1) / b->bt);
+            F.v[j] = views[j];
+            F.slab[j] = FusedSlab{c->d_slab_site, c->d_slab_side, static_cast<int>(n_slab),
+                                  static_cast<float>(c->params.rho_in), static_cast<float>(c->params.rho_out)};
+        }
+        b->fused_ready = true;
+    }
     LBPM_BCK(b, cudaStreamSynchronize(b->stream));
     b->dirty = false;
     return LBPM_OK;
@@ -224,6 +264,63 @@ bool batch_sum_form(const lbpm_batch* b) {
     for (const lbpm_ctx* c : b->jobs)
         if (!sum_form_capable(c)) return false;
     return true;
+}
+
+// Whether the batch runs the fused persistent kernel (chosen with blocks per
+// SM -2, and possible for this batch).
+bool use_fused(const lbpm_batch* b) { return b->bps[0] == -2 && b->bps[1] == -2 && b->fused_ready; }
+
+// One fused launch: clear its barrier and tile counters, then the cooperative
+// grid of as many blocks as fit the GPU at once.
+cudaError_t fused_launch(lbpm_batch* b, int kind, cudaStream_t s) {
+    const bool h = b->precision == LBPM_FP16;
+    const int per_sm = batch_fused_blocks_per_sm(kind, h, b->bt);
+    if (per_sm < 1) return cudaErrorCooperativeLaunchTooLarge;
+    cudaError_t e = cudaMemsetAsync(b->d_ctl, 0, sizeof(unsigned) * kFusedCtl, s);
+    if (e == cudaSuccess) e = launch_batch_fused(kind, h, b->bt, static_cast<unsigned>(per_sm * b->n_sm), s, *b->fused);
+    return e;
+}
+
+lbpm_status capture_fused(lbpm_batch* b, int kind, cudaGraphExec_t* out) {
+    if (*out) cudaGraphExecDestroy(*out);
+    *out = nullptr;
+    if (!b->cap_stream) LBPM_BCK(b, cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking));
+    LBPM_BCK(b, cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
+    const cudaError_t el = fused_launch(b, kind, b->cap_stream);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(b->cap_stream, &g);
+    if (el != cudaSuccess) e = el;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(out, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) return bfail_cuda(b, "fused batch graph capture", e);
+    return LBPM_OK;
+}
+
+// lbpm_batch_advance with the fused kernel: in the sum form one launch for the
+// first step, a graph of two middle steps replayed, one launch for the last
+// step; in the population form a graph of two steps replayed.
+lbpm_status batch_advance_fused(lbpm_batch* b, long long nsteps) {
+    if (batch_sum_form(b)) {
+        LBPM_BCK(b, fused_launch(b, kFusedSumFirst, b->stream));
+        if (nsteps > 2) {
+            if (!b->fused_graph) {
+                lbpm_status s = capture_fused(b, kFusedSumMid, &b->fused_graph);
+                if (s) return s;
+            }
+            for (long long k = 2; k < nsteps; k += 2) LBPM_BCK(b, cudaGraphLaunch(b->fused_graph, b->stream));
+        }
+        LBPM_BCK(b, fused_launch(b, kFusedSumLast, b->stream));
+        b->launches += 2 + (nsteps - 2) / 2;
+    } else {
+        if (!b->fused_graph) {
+            lbpm_status s = capture_fused(b, kFusedPop, &b->fused_graph);
+            if (s) return s;
+        }
+        for (long long k = 0; k < nsteps; k += 2) LBPM_BCK(b, cudaGraphLaunch(b->fused_graph, b->stream));
+        b->launches += nsteps / 2;
+    }
+    for (lbpm_ctx* c : b->jobs) c->step += nsteps;
+    return LBPM_OK;
 }
 
 int kernels_per_bundle(const lbpm_batch* b) {
@@ -300,6 +397,9 @@ lbpm_status lbpm_batch_destroy(lbpm_batch* b) {
     bfree(b, b->d_mbegin);
     bfree(b, b->d_partials);
     bfree(b, b->d_out);
+    bfree(b, b->d_ctl);
+    bfree(b, b->d_err);
+    delete b->fused;
     delete b;
     return LBPM_OK;
 }
@@ -377,6 +477,7 @@ lbpm_status lbpm_batch_advance(lbpm_batch* b, long long nsteps) {
     }
     if (b->jobs.empty() || nsteps == 0) return LBPM_OK;
     if (b->dirty && (s = rebuild(b))) return s;
+    if (use_fused(b)) return batch_advance_fused(b, nsteps);
     if (batch_sum_form(b)) return batch_advance_sum(b, nsteps);
     if (!b->graph && (s = capture(b, kBPop, 0, &b->graph))) return s;
     for (long long k = 0; k < nsteps; k += 2) LBPM_BCK(b, cudaGraphLaunch(b->graph, b->stream));
@@ -400,8 +501,16 @@ lbpm_status lbpm_batch_measure(lbpm_batch* b, lbpm_measures* out) {
                                      b->d_mtiles, b->n_mtiles, b->d_partials, b->d_mbegin, J, b->d_out));
     std::vector<double> S(static_cast<size_t>(NSUM) * J);
     LBPM_BCK(b, cudaMemcpyAsync(S.data(), b->d_out, sizeof(double) * S.size(), cudaMemcpyDeviceToHost, b->stream));
+    int err = 0;
+    if (b->d_err) LBPM_BCK(b, cudaMemcpyAsync(&err, b->d_err, sizeof(int), cudaMemcpyDeviceToHost, b->stream));
     LBPM_BCK(b, cudaStreamSynchronize(b->stream));
     b->launches += 2;
+    if (err) {
+        LBPM_BCK(b, cudaMemsetAsync(b->d_err, 0, sizeof(int), b->stream));
+        for (lbpm_ctx* c : b->jobs) c->unstable = true;
+        return bfail(b, LBPM_E_TIMEOUT, "a grid barrier of the fused batch kernel gave up waiting; the jobs' states are "
+                                        "incomplete (re-initialise or restore them)");
+    }
     lbpm_status st = LBPM_OK;
     for (int j = 0; j < J; ++j) {
         fill_measures(b->jobs[j], S.data() + static_cast<size_t>(NSUM) * j, out + j);
@@ -419,7 +528,10 @@ lbpm_status lbpm_batch_set_launch(lbpm_batch* b, int threads, int bps_phase, int
     if (s) return s;
     if (threads != 128 && threads != 256 && threads != 512)
         return bfail(b, LBPM_E_INVALID, "threads per block must be 128, 256 or 512");
-    if (bps_phase < -1 || bps_collide < -1) return bfail(b, LBPM_E_INVALID, "blocks per SM must be >= -1");
+    if (bps_phase < -2 || bps_collide < -2) return bfail(b, LBPM_E_INVALID, "blocks per SM must be >= -2");
+    if ((bps_phase == -2) != (bps_collide == -2))
+        return bfail(b, LBPM_E_INVALID, "the fused kernel (-2) covers both passes: give -2 for both");
+    if (bps_phase == -2 && threads == 512) return bfail(b, LBPM_E_INVALID, "the fused kernel runs 128 or 256 threads");
     LBPM_BCK(b, cudaStreamSynchronize(b->stream));
     if (threads != b->bt) b->dirty = true;
     b->bt = threads;
@@ -450,9 +562,16 @@ lbpm_status lbpm_batch_tune(lbpm_batch* b, int steps_per_candidate, int* threads
         const bool h = b->precision == LBPM_FP16;
         for (int bt : {128, 256, 512}) {
             const int occ = std::min(batch_max_blocks(0, h, bt), batch_max_blocks(1, h, bt));
-            // one block per tile, then persistent grids at the occupancy limit, half of it, a quarter
-            for (int frac : {-1, 4, 2, 1}) {
-                const int bps = frac < 0 ? -1 : std::max(1, occ * frac / 4);
+            // the fused persistent kernel (where it applies), one block per tile,
+            // then persistent grids at the occupancy limit, half of it, a quarter
+            for (int frac : {-2, -1, 4, 2, 1}) {
+                if (frac == -2) {
+                    if (bt == 512 || b->jobs.size() > static_cast<size_t>(kFusedJobs)) continue;
+                    bool ok = true;
+                    for (const lbpm_ctx* c : b->jobs) ok = ok && c->params.reservoir_z <= 1;
+                    if (!ok) continue;
+                }
+                const int bps = frac < 0 ? frac : std::max(1, occ * frac / 4);
                 if ((s = lbpm_batch_set_launch(b, bt, bps, bps))) break;
                 if ((s = lbpm_batch_advance(b, 2))) break;  // capture + warm up
                 cudaEventRecord(e0, b->stream);
@@ -478,6 +597,34 @@ lbpm_status lbpm_batch_tune(lbpm_batch* b, int steps_per_candidate, int* threads
     if (threads) *threads = best[0];
     if (bps_phase) *bps_phase = best[1];
     if (bps_collide) *bps_collide = best[2];
+    return LBPM_OK;
+}
+
+lbpm_status lbpm_batch_check_barrier(lbpm_batch* b, int missing, double limit_s) {
+    lbpm_status s = enter(b);
+    if (s) return s;
+    if (missing < 0 || !(limit_s > 0.0) || limit_s > 10.0)
+        return bfail(b, LBPM_E_INVALID, "missing must be >= 0 and the limit in (0, 10] s");
+    unsigned* ctl = static_cast<unsigned*>(balloc(b, sizeof(unsigned) * 2));
+    int* err = static_cast<int*>(balloc(b, sizeof(int)));
+    if (!ctl || !err) {
+        bfree(b, ctl);
+        bfree(b, err);
+        return bfail(b, LBPM_E_OOM, "barrier self-test allocation failed");
+    }
+    int h_err = 0;
+    const unsigned grid = static_cast<unsigned>(b->n_sm);
+    cudaError_t e = cudaMemsetAsync(ctl, 0, sizeof(unsigned) * 2, b->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, sizeof(int), b->stream);
+    if (e == cudaSuccess)
+        e = launch_barrier_probe(grid, grid + static_cast<unsigned>(missing),
+                                 static_cast<unsigned long long>(limit_s * 1e9), ctl, err, b->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    bfree(b, ctl);
+    bfree(b, err);
+    if (e != cudaSuccess) return bfail_cuda(b, "barrier self-test", e);
+    if (h_err) return bfail(b, LBPM_E_TIMEOUT, "the grid barrier's wait ran out");
     return LBPM_OK;
 }
 

@@ -78,8 +78,9 @@ def test_batch_matches_alone(precision):
     b.close()
 
 
+@pytest.mark.parametrize("mode", ["launches", "fused"])
 @pytest.mark.parametrize("precision", ["fp32", "fp16"])
-def test_batched_jobs_match_the_oracle(precision):
+def test_batched_jobs_match_the_oracle(precision, mode):
     """Every job of the uneven set (three periodicities, two viscosity pairs,
     a reservoir job) advanced in one batch against its own FP64 oracle: one
     even plus one odd step per distribution (FP32: 2 x 1e-6 max(|o|, w_q),
@@ -106,6 +107,8 @@ def test_batched_jobs_match_the_oracle(precision):
     b = lbm.Batch()
     for d in doms:
         b.add(d)
+    if mode == "fused":
+        b.set_launch(256, -2, -2)
     b.advance(2)
     for j, (d, o) in enumerate(zip(doms, refs)):
         o.step(2)
@@ -265,4 +268,67 @@ def test_batch_rejects_bad_jobs():
         b.add(odd)                 # odd step
     with pytest.raises(lbm.LBPMError):
         b.advance(3)               # bundles are even
+    b.close()
+
+
+@pytest.mark.parametrize("form", ["auto", "populations"])
+@pytest.mark.parametrize("precision", ["fp32", "fp16"])
+def test_fused_kernel_matches_separate_launches(precision, form):
+    """The fused persistent kernel (one cooperative launch per bundle: phase
+    pass, collision and reservoir reset of every job, grid barriers between the
+    passes) against the separate launches, on the uneven set with its reservoir
+    job, in both step forms and at 128 and 256 threads: the same device
+    functions compiled into another kernel, so agreement to fp32 round-off
+    (1e-5 per distribution after 24 steps, as for batched against alone)."""
+    import paper_2007_12266_gb300 as lbm
+    specs = _jobs()
+    results = {}
+    for shape in ((256, -1), (256, -2), (128, -2)):
+        doms = [_make(s, precision) for s in specs]
+        for d in doms:
+            d.set_step_form(form)
+        b = lbm.Batch()
+        for d in doms:
+            b.add(d)
+        b.set_launch(shape[0], shape[1], shape[1])
+        n0 = b.launch_count
+        b.advance(10)
+        b.advance(14)
+        if shape[1] == -2:
+            # one launch per two steps; the sum form launches the first and the
+            # last step of each call alone: (1 + 4 + 1) + (1 + 6 + 1)
+            assert b.launch_count - n0 == (14 if form == "auto" else 12), b.launch_count - n0
+        assert all(m["status"] == 0 for m in b.measure())
+        results[shape] = [[d.distributions(k).astype(np.float64) for k in ("f", "a", "b")] for d in doms]
+        b.close()
+        for d in doms:
+            d.close()
+    base = results[(256, -1)]
+    for shape in ((256, -2), (128, -2)):
+        for j, (ga, gb) in enumerate(zip(base, results[shape])):
+            for which, x, y, floor in zip("fab", ga, gb, (T19, W7, W7)):
+                err = np.abs(x - y) / np.maximum(np.abs(x), floor[:, None])
+                assert err.max() <= 1e-5, (shape, j, which, err.max())
+
+
+def test_fused_barrier_wait_is_bounded():
+    """The fused kernel's grid barrier gives up after its limit: a barrier
+    that expects one arrival more than there are blocks (a flag nothing sets)
+    ends with LBPM_E_TIMEOUT after the limit, and the GPU stays usable."""
+    import time
+
+    import paper_2007_12266_gb300 as lbm
+    b = lbm.Batch()
+    assert b.check_barrier(0, 0.5) is True          # every block arrives: completes
+    t0 = time.perf_counter()
+    assert b.check_barrier(1, 0.05) is False        # one arrival never comes: the wait runs out
+    assert time.perf_counter() - t0 < 5.0
+    assert b.check_barrier(0, 0.5) is True          # the context still works
+    specs = _jobs()[:2]
+    doms = [_make(s, "fp32") for s in specs]
+    for d in doms:
+        b.add(d)
+    b.set_launch(256, -2, -2)
+    b.advance(4)
+    assert all(m["status"] == 0 for m in b.measure())
     b.close()
