@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "internal.h"
+#include "batch_fused.h"
 
 using namespace lbm;
 
@@ -195,7 +196,9 @@ lbpm_status rebuild(lbpm_batch* b) {
             const lbpm_ctx* c = b->jobs[j];
             const long long n_slab = c->params.reservoir_z == 1 ? c->n_slab : 0;
             const long long counts[3] = {c->N + c->H, c->N, n_slab};
-            for (int k = 0; k < 3; ++k) F.tiles[k][j + 1] = F.tiles[k][j] + static_cast<int>((counts[k] + b->bt - 1) / b->bt);
+            const long long per_tile[3] = {static_cast<long long>(b->bt) * kFusedPhasePer, b->bt, b->bt};
+            for (int k = 0; k < 3; ++k)
+                F.tiles[k][j + 1] = F.tiles[k][j] + static_cast<int>((counts[k] + per_tile[k] - 1) / per_tile[k]);
             F.v[j] = views[j];
             F.slab[j] = FusedSlab{c->d_slab_site, c->d_slab_side, static_cast<int>(n_slab),
                                   static_cast<float>(c->params.rho_in), static_cast<float>(c->params.rho_out)};

@@ -193,36 +193,6 @@ struct BatchLaunch {
 // 0 = populations, 1 = sums from the phase pass, 2 = sums from the sums.
 cudaError_t launch_batch(int kernel, int form, int par, bool fp16, int bt, unsigned grid, cudaStream_t s,
                          const BatchLaunch& p);
-// Fused batched form (batch_fused.cu): one cooperative persistent launch per
-// bundle runs the phase pass, the collision and the reservoir reset of every
-// job, with bounded grid barriers between the passes.
-constexpr int kFusedJobs = 112;   // jobs per fused launch (the table lives in the parameter space)
-enum FusedStepKind { kFusedPop = 0, kFusedSumFirst = 1, kFusedSumMid = 2, kFusedSumLast = 3 };
-constexpr int kFusedCtl = 2 + 6;  // barrier arrivals and generation, then one tile counter per pass
-struct FusedSlab {
-    const int* site;
-    const signed char* side;
-    int n;
-    float rho_in, rho_out;
-};
-struct FusedLaunch {
-    int n_jobs;
-    int tiles[3][kFusedJobs + 1];    // first tile of each job: phase entries, sites, slab sites
-    unsigned long long limit_ns;     // bound of a barrier wait
-    unsigned* ctl;                   // [kFusedCtl] zeroed before each launch
-    int* err;                        // set when a barrier wait gave up
-    DomainView v[kFusedJobs];
-    FusedSlab slab[kFusedJobs];
-};
-// kind: FusedStepKind (pop: two steps from an even one; sum first: one step
-// from an even one; sum middle: two steps from an odd one; sum last: one step
-// at an odd one); bt = 128 or 256 threads per block.
-cudaError_t launch_batch_fused(int kind, bool fp16, int bt, unsigned grid, cudaStream_t s, const FusedLaunch& p);
-int batch_fused_blocks_per_sm(int kind, bool fp16, int bt);
-// One lone barrier of `grid` blocks waiting for `expected` arrivals (self-test).
-cudaError_t launch_barrier_probe(unsigned grid, unsigned expected, unsigned long long limit_ns, unsigned* ctl, int* err,
-                                 cudaStream_t s);
-
 cudaError_t launch_batch_measure(bool fp16, unsigned grid, cudaStream_t s, const DomainView* v, const int* parity,
                                  const BatchTile* t, int nt, double* partials, const int* tile_begin, int n_jobs,
                                  double* out);
