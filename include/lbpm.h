@@ -370,15 +370,15 @@ lbpm_status lbpm_batch_advance(lbpm_batch* batch, long long nsteps);
  * if a grid barrier of the fused kernel (below) gave up waiting since the last
  * measure (the jobs are then flagged unstable: their states are incomplete). */
 lbpm_status lbpm_batch_measure(lbpm_batch* batch, lbpm_measures* out);
-/* Launch shape: threads per block (128, 256 or 512) and resident blocks per
+/* Launch shape: threads per block (128, 192, 256 or 512) and resident blocks per
  * SM of the persistent phase and collide grids (0 = occupancy limit, -1 = no
  * persistent grid: one block per tile, scheduled by the hardware; -2 for both
  * = one fused persistent kernel per bundle of steps: a cooperative grid of
  * every block that fits the GPU runs the phase pass, the collision and the
  * reservoir reset of all jobs, taking tiles from an atomic counter in each
- * pass, with a grid barrier between passes whose wait gives up after 2 s; 128
- * or 256 threads, batches of up to 112 jobs without pressure or flux faces,
- * other batches keep the separate launches). A new batch starts at 256 threads
+ * pass, with a grid barrier between passes whose wait gives up after 2 s; 128,
+ * 192 or 256 threads, batches of up to 112 jobs without pressure or flux faces,
+ * other batches keep the separate launches). A new batch starts at 192 threads
  * and -1 for both kernels. */
 lbpm_status lbpm_batch_set_launch(lbpm_batch* batch, int threads, int blocks_per_sm_phase,
                                   int blocks_per_sm_collide);

@@ -138,6 +138,7 @@ cudaError_t launch_batch(int kernel, int form, int par, bool fp16, int bt, unsig
     if (p.n_jobs == 0 || p.tile_begin[p.n_jobs] == 0) return cudaSuccess;
     switch (bt) {
     case 128: return batch_bt<128>(kernel, form, par, fp16, grid, s, p);
+    case 192: return batch_bt<192>(kernel, form, par, fp16, grid, s, p);
     case 512: return batch_bt<512>(kernel, form, par, fp16, grid, s, p);
     default: return batch_bt<256>(kernel, form, par, fp16, grid, s, p);
     }
@@ -204,7 +205,7 @@ int batch_max_blocks(int kernel, bool fp16, int bt) {
     f = kernel == 0 ? (fp16 ? (const void*)k_batch_phase<1, StoreF16, BT> : (const void*)k_batch_phase<1, StoreF32, BT>) \
                     : (fp16 ? (const void*)k_batch_collide<1, StoreF16, 2, BT>                                \
                             : (const void*)k_batch_collide<1, StoreF32, 2, BT>);
-    if (bt == 128) { LBPM_PICK(128) } else if (bt == 512) { LBPM_PICK(512) } else { LBPM_PICK(256) }
+    if (bt == 128) { LBPM_PICK(128) } else if (bt == 192) { LBPM_PICK(192) } else if (bt == 512) { LBPM_PICK(512) } else { LBPM_PICK(256) }
 #undef LBPM_PICK
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f, bt, 0) != cudaSuccess) {
         cudaGetLastError();

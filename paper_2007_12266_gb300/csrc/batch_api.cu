@@ -37,10 +37,12 @@ struct lbpm_batch {
     bool dirty = true;
     // launch shape
     // resident blocks per SM of the persistent grids (0 = occupancy limit, -1 =
-    // one block per tile). The default is the autotuner's choice on GB300 for
-    // mixed job sizes in both storages: the hardware block scheduler balances
-    // uneven tiles better than a static round-robin over persistent blocks.
-    int bt = 256;
+    // one block per tile). The default is the fastest shape measured on GB300
+    // for mixed job sizes in both storages: one block per tile (the hardware
+    // block scheduler balances uneven tiles better than a static round-robin
+    // over persistent blocks) of 192 threads (six blocks, 36 warps per SM at 56
+    // registers for the collision).
+    int bt = 192;
     int bps[2] = {-1, -1};
     int n_sm = 0;
     // bundle graphs (2 timesteps): graph = population form; sum_graph = two
@@ -176,7 +178,7 @@ lbpm_status rebuild(lbpm_batch* b) {
                                     cudaMemcpyHostToDevice, b->stream));
     // fused table: up to kFusedJobs jobs, no pressure or flux faces
     b->fused_ready = false;
-    bool fusable = J > 0 && J <= kFusedJobs && (b->bt == 128 || b->bt == 256);
+    bool fusable = J > 0 && J <= kFusedJobs && b->bt != 512;
     for (const lbpm_ctx* c : b->jobs) fusable = fusable && c->params.reservoir_z <= 1;
     if (fusable) {
         if (!b->fused) b->fused = new (std::nothrow) FusedLaunch;
@@ -196,7 +198,7 @@ lbpm_status rebuild(lbpm_batch* b) {
             const lbpm_ctx* c = b->jobs[j];
             const long long n_slab = c->params.reservoir_z == 1 ? c->n_slab : 0;
             const long long counts[3] = {c->N + c->H, c->N, n_slab};
-            const long long per_tile[3] = {static_cast<long long>(b->bt) * kFusedPhasePer, b->bt, b->bt};
+            const long long per_tile[3] = {static_cast<long long>(b->bt) * fused_phase_per(b->bt), b->bt, b->bt};
             for (int k = 0; k < 3; ++k)
                 F.tiles[k][j + 1] = F.tiles[k][j] + static_cast<int>((counts[k] + per_tile[k] - 1) / per_tile[k]);
             F.v[j] = views[j];
@@ -529,12 +531,12 @@ lbpm_status lbpm_batch_measure(lbpm_batch* b, lbpm_measures* out) {
 lbpm_status lbpm_batch_set_launch(lbpm_batch* b, int threads, int bps_phase, int bps_collide) {
     lbpm_status s = enter(b);
     if (s) return s;
-    if (threads != 128 && threads != 256 && threads != 512)
-        return bfail(b, LBPM_E_INVALID, "threads per block must be 128, 256 or 512");
+    if (threads != 128 && threads != 192 && threads != 256 && threads != 512)
+        return bfail(b, LBPM_E_INVALID, "threads per block must be 128, 192, 256 or 512");
     if (bps_phase < -2 || bps_collide < -2) return bfail(b, LBPM_E_INVALID, "blocks per SM must be >= -2");
     if ((bps_phase == -2) != (bps_collide == -2))
         return bfail(b, LBPM_E_INVALID, "the fused kernel (-2) covers both passes: give -2 for both");
-    if (bps_phase == -2 && threads == 512) return bfail(b, LBPM_E_INVALID, "the fused kernel runs 128 or 256 threads");
+    if (bps_phase == -2 && threads == 512) return bfail(b, LBPM_E_INVALID, "the fused kernel runs 128, 192 or 256 threads");
     LBPM_BCK(b, cudaStreamSynchronize(b->stream));
     if (threads != b->bt) b->dirty = true;
     b->bt = threads;
@@ -563,7 +565,7 @@ lbpm_status lbpm_batch_tune(lbpm_batch* b, int steps_per_candidate, int* threads
         LBPM_BCK(b, cudaEventCreate(&e1));
         float best_ms = 1e30f;
         const bool h = b->precision == LBPM_FP16;
-        for (int bt : {128, 256, 512}) {
+        for (int bt : {128, 192, 256, 512}) {
             const int occ = std::min(batch_max_blocks(0, h, bt), batch_max_blocks(1, h, bt));
             // the fused persistent kernel (where it applies), one block per tile,
             // then persistent grids at the occupancy limit, half of it, a quarter

@@ -126,21 +126,22 @@ __global__ void __launch_bounds__(BT, 1152 / BT) k_batch_fused(const __grid_cons
         if (!go) return;
         // phase pass (and, at the first step of a sum-form run, clearing the
         // sums the collision accumulates into)
-        // (kFusedPhasePer independent entries per thread: the pass is
+        // (fused_phase_per(BT) independent entries per thread: the pass is
         // latency-bound, and the fused kernel runs fewer warps than the
         // separate phase kernel because it holds the collision's registers)
         fused_pass(p, pass++, p.tiles[0], [&](int j, int tj) {
             const DomainView& d = p.v[j];
-            const int i0 = tj * BT * kFusedPhasePer + static_cast<int>(threadIdx.x);
+            constexpr int PER = fused_phase_per(BT);
+            const int i0 = tj * BT * PER + static_cast<int>(threadIdx.x);
             if constexpr (K::kPhase == 0) {
                 #pragma unroll
-                for (int k = 0; k < kFusedPhasePer; ++k) phase_thread<PAR, S>(d, i0 + k * BT);
+                for (int k = 0; k < PER; ++k) phase_thread<PAR, S>(d, i0 + k * BT);
             } else {
-                phase_sum_thread<PAR, K::kPhase == 2, kFusedPhasePer>(d, i0, BT);
+                phase_sum_thread<PAR, K::kPhase == 2, PER>(d, i0, BT);
             }
             if constexpr (K::kClearTargets) {
                 #pragma unroll
-                for (int k = 0; k < kFusedPhasePer; ++k)
+                for (int k = 0; k < PER; ++k)
                     if (i0 + k * BT < d.n_sites) d.acc[PAR ^ 1][i0 + k * BT] = 0ull;
             }
         });
@@ -211,14 +212,17 @@ static_assert(sizeof(FusedLaunch) <= 32000, "fused job table must fit the kernel
 cudaError_t launch_batch_fused(int kind, bool fp16, int bt, unsigned grid, cudaStream_t s, const FusedLaunch& p) {
     if (bt == 128)
         return fp16 ? launch_fused_bt<StoreF16, 128>(kind, grid, s, p) : launch_fused_bt<StoreF32, 128>(kind, grid, s, p);
+    if (bt == 192)
+        return fp16 ? launch_fused_bt<StoreF16, 192>(kind, grid, s, p) : launch_fused_bt<StoreF32, 192>(kind, grid, s, p);
     return fp16 ? launch_fused_bt<StoreF16, 256>(kind, grid, s, p) : launch_fused_bt<StoreF32, 256>(kind, grid, s, p);
 }
 
 int batch_fused_blocks_per_sm(int kind, bool fp16, int bt) {
-    const void* f = bt == 128 ? (fp16 ? fused_fn<StoreF16, 128>(kind) : fused_fn<StoreF32, 128>(kind))
-                              : (fp16 ? fused_fn<StoreF16, 256>(kind) : fused_fn<StoreF32, 256>(kind));
+    const void* f = bt == 128   ? (fp16 ? fused_fn<StoreF16, 128>(kind) : fused_fn<StoreF32, 128>(kind))
+                    : bt == 192 ? (fp16 ? fused_fn<StoreF16, 192>(kind) : fused_fn<StoreF32, 192>(kind))
+                                : (fp16 ? fused_fn<StoreF16, 256>(kind) : fused_fn<StoreF32, 256>(kind));
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f, bt == 128 ? 128 : 256, 0) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f, bt == 128 || bt == 192 ? bt : 256, 0) != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }

@@ -10,7 +10,10 @@ namespace lbm {
 constexpr int kFusedJobs = 112;   // jobs per fused launch (the table lives in the parameter space)
 enum FusedStepKind { kFusedPop = 0, kFusedSumFirst = 1, kFusedSumMid = 2, kFusedSumLast = 3 };
 constexpr int kFusedCtl = 2 + 6;  // barrier arrivals and generation, then one tile counter per pass
-constexpr int kFusedPhasePer = 8;  // phase entries per thread in the fused kernel (a phase tile is 8 x threads; 16 spill)
+// phase entries per thread in the fused kernel (a phase tile is that many x
+// threads): 8 at 256 threads (64 registers; 16 spill), 4 at 128 and 192 (56
+// registers; 8 spill)
+constexpr int fused_phase_per(int bt) { return bt >= 256 ? 8 : 4; }
 struct FusedSlab {
     const int* site;
     const signed char* side;
@@ -28,7 +31,7 @@ struct FusedLaunch {
 };
 // kind: FusedStepKind (pop: two steps from an even one; sum first: one step
 // from an even one; sum middle: two steps from an odd one; sum last: one step
-// at an odd one); bt = 128 or 256 threads per block.
+// at an odd one); bt = 128, 192 or 256 threads per block.
 cudaError_t launch_batch_fused(int kind, bool fp16, int bt, unsigned grid, cudaStream_t s, const FusedLaunch& p);
 int batch_fused_blocks_per_sm(int kind, bool fp16, int bt);
 // One lone barrier of `grid` blocks waiting for `expected` arrivals (self-test).
