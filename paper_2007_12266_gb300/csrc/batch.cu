@@ -1,18 +1,21 @@
 // Batched form: many independent domains (jobs) advanced together.
 //
-// Each job keeps its own context and device arrays. A batch builds a device
-// table of the jobs' views and a global list of tiles (job, first thread) over
-// all jobs, and advances every job with ONE persistent launch per phase: the
-// blocks of the phase kernel, then of the fused collide-stream kernel, walk
-// the whole tile list in a fixed round-robin order. Step bundles are captured
-// into a CUDA graph. Bundles hold an even number of steps, so every job is at
-// an even step at a bundle boundary and the AA parity of each launch is a
-// compile-time constant for the whole batch.
+// Each job keeps its own context and device arrays. A batch builds a table of
+// the jobs' views and of the first tile of each job (passed by value in the
+// kernel's parameter space), and advances every job with ONE launch per pass:
+// the phase kernel, then the fused collide-stream kernel, over the tiles of
+// all jobs, either one block per tile (the default) or a persistent grid whose
+// blocks walk the tile list round-robin. Step bundles are captured into a CUDA
+// graph. Bundles hold an even number of steps, so every job is at an even
+// step at a bundle boundary and the AA parity of each launch is a
+// compile-time constant for the whole batch. (The alternative of one
+// cooperative kernel for every pass of a bundle is in batch_fused.cu.)
 //
-// The launch shape (threads per block, resident blocks per SM) is picked by a
-// small autotuner that times candidates on real steps (every candidate
-// computes identical results, so tuning advances the simulation normally) and
-// caches the winner per GPU, precision and size class.
+// The launch shape (threads per block, resident blocks per SM or one block
+// per tile, or the fused kernel) is picked by a small autotuner that times
+// candidates on real steps (every candidate computes identical results, so
+// tuning advances the simulation normally) and caches the winner per GPU,
+// precision and size class.
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
