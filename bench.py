@@ -268,7 +268,8 @@ def _domain(lbm, w, precision, device):
 
 
 def bench_batched(jobs, precision, steps, device):
-    """Batched form: all jobs in one persistent launch per phase, tuned shape."""
+    """Batched form: all jobs in one launch per pass (or one fused launch per
+    bundle), at the shape the autotuner picks."""
     import torch
 
     import paper_2007_12266_gb300 as lbm

@@ -331,8 +331,9 @@ lbpm_status lbpm_kernel_timing(lbpm_ctx* ctx, double* ms_collide, long long* n_c
  * Batched form: several jobs (independent contexts on one GPU, same storage
  * precision) advanced together. Every timestep of the whole batch is ONE
  * launch of the phase pass and ONE of the fused collide-stream kernel, both
- * over a list of tiles that covers all jobs' sites; bundles of two steps are
- * replayed from a CUDA graph. Inside a call of two or more steps the
+ * over a list of tiles that covers all jobs' sites (or, with the fused launch
+ * shape of lbpm_batch_set_launch, one kernel runs every pass of a bundle);
+ * bundles of two steps are replayed from a CUDA graph. Inside a call of two or more steps the
  * components travel as per-site sums when every job allows it (see
  * lbpm_set_step_form). Each job's results agree with
  * advancing it alone to fp32 rounding (1e-5 relative per distribution after

@@ -415,7 +415,8 @@ class Domain:
 
 class Batch:
     """Several Domains (same GPU, same storage precision) advanced together by
-    one persistent launch per phase over all their sites (lbpm_batch_* ABI).
+    one launch per pass over all their sites, or one fused cooperative launch
+    per bundle of steps (lbpm_batch_* ABI).
     Results agree with advancing each domain alone to fp32 rounding (the
     batched kernels are compiled separately, so multiply-add contraction may
     differ); two batched runs of the same jobs are bit-identical."""

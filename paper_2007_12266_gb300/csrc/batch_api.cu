@@ -1,5 +1,6 @@
 // C ABI of the batched form (declared in include/lbpm.h): a batch of job
-// contexts advanced together by the persistent batch kernels (batch.cu).
+// contexts advanced together by the batch kernels (batch.cu: one launch per
+// pass) or the fused kernel (batch_fused.cu: one launch per bundle).
 #include <algorithm>
 #include <new>
 #include <cmath>
