@@ -267,9 +267,10 @@ def _domain(lbm, w, precision, device):
     return d
 
 
-def bench_batched(jobs, precision, steps, device):
+def bench_batched(jobs, precision, steps, device, launch=None):
     """Batched form: all jobs in one launch per pass (or one fused launch per
-    bundle), at the shape the autotuner picks."""
+    bundle), at the shape the autotuner picks, or at `launch` = (threads,
+    blocks per SM) when given."""
     import torch
 
     import paper_2007_12266_gb300 as lbm
@@ -277,7 +278,11 @@ def bench_batched(jobs, precision, steps, device):
     b = lbm.Batch(device=device)
     for d in doms:
         b.add(d)
-    shape = b.tune(steps_per_candidate=4)
+    if launch is None:
+        shape = b.tune(steps_per_candidate=4)
+    else:
+        b.set_launch(launch[0], launch[1], launch[1])
+        shape = (launch[0], launch[1], launch[1])
     b.advance(20)
     stream = torch.cuda.current_stream(device)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -637,6 +642,11 @@ def bench_gpu(args):
                 "sat_mass": m16["sat_mass"], "flux_z": m16["flux"][2]}
 
     batched = None
+    batched_launch = None
+    if args.batched_launch:
+        batched_launch = tuple(int(x) for x in args.batched_launch.split(":"))
+        if len(batched_launch) != 2:
+            raise SystemExit("--batched-launch takes THREADS:BLOCKS_PER_SM")
     if not args.no_batched:
         try:
             # the jobs are independent: each rank runs its round-robin share
@@ -645,7 +655,7 @@ def bench_gpu(args):
             batched = {"workload": f"{args.batched_jobs} sphere-pack jobs, L in {{64..192}}, porosity U[0.15,0.35]"
                                    + (f", {world} ranks, round-robin shards" if world > 1 else "")}
             for bprec in ("fp32", "fp16"):
-                r = bench_batched(jobs, bprec, args.batched_steps, local_rank)
+                r = bench_batched(jobs, bprec, args.batched_steps, local_rank, batched_launch)
                 ms_all, su_all = reduce_over_ranks(r["ms"], float(r["n_sites"] * r["steps"]), world, dev)
                 r["value"] = su_all / (ms_all * 1e-3) / 1e6
                 r["ms"] = ms_all
@@ -767,6 +777,9 @@ def main():
     ap.add_argument("--no-serving", action="store_true", help="skip the serving run")
     ap.add_argument("--batched-jobs", type=int, default=64, help="jobs of the batched set")
     ap.add_argument("--batched-steps", type=int, default=2000, help="timesteps of the batched set")
+    ap.add_argument("--batched-launch", default=None,
+                    help="launch shape of the batched set as THREADS:BLOCKS_PER_SM (-1 one block per tile, "
+                         "-2 fused kernel) instead of the autotuner's choice")
     ap.add_argument("--serving-jobs", type=int, default=16, help="arrivals of the serving trace")
     ap.add_argument("--serving-max-steps", type=int, default=10000, help="step ceiling of a serving job")
     args = ap.parse_args()

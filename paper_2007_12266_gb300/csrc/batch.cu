@@ -24,6 +24,7 @@
 #include <string>
 #include <vector>
 
+#include "batch.h"
 #include "measure_kernels.cuh"
 
 namespace lbm {
@@ -151,7 +152,9 @@ namespace {
 
 static_assert(sizeof(DomainView) % sizeof(int) == 0, "view copied as ints");
 
-// Per-tile fp64 partial sums of the measures; each job's parity is read per tile.
+// Per-tile fp64 partial sums of the measures (kBatchMeasureTile sites per
+// tile, kBatchMeasureTile / BT per thread, strided by BT so that loads
+// coalesce); each job's parity is read per tile.
 template <class S, int BT>
 __global__ void __launch_bounds__(BT) k_batch_measure(const DomainView* views, const int* parity,
                                                       const BatchTile* tiles, int n_tiles, double* partials) {
@@ -164,8 +167,9 @@ __global__ void __launch_bounds__(BT) k_batch_measure(const DomainView* views, c
         if (threadIdx.x == 0) par = parity[tl.job];
         __syncthreads();
         AccF64 acc[NSUM];
-        const int n = tl.first + threadIdx.x;
-        if (n < sv.n_sites) {
+        for (int k = 0; k < kBatchMeasureTile / BT; ++k) {
+            const int n = tl.first + k * BT + static_cast<int>(threadIdx.x);
+            if (n >= sv.n_sites) break;
             if (par) measure_site<1, S>(sv, n, acc);
             else measure_site<0, S>(sv, n, acc);
         }

@@ -1,11 +1,20 @@
-// Fused batched form (batch_fused.cu): one cooperative persistent launch per
-// bundle runs the phase pass, the collision and the reservoir reset of every
-// job, with bounded grid barriers between the passes. Declared apart from the
-// step kernels' shared header, which it only uses.
+// Batched form: declarations shared by batch.cu, batch_fused.cu and
+// batch_api.cu, apart from the step kernels' shared header (internal.h),
+// which they only use.
 #pragma once
 #include "internal.h"
 
 namespace lbm {
+
+// Sites of one tile of the batched basic analysis: 32 per thread of a
+// 256-thread block, each thread summing its sites in compensated fp32 before
+// the block's one fp64 reduction (as the single-domain analysis does; within
+// the accumulator's 64-site bound).
+constexpr int kBatchMeasureTile = 256 * 32;
+
+// Fused batched form (batch_fused.cu): one cooperative persistent launch per
+// bundle runs the phase pass, the collision and the reservoir reset of every
+// job, with bounded grid barriers between the passes.
 
 constexpr int kFusedJobs = 112;   // jobs per fused launch (the table lives in the parameter space)
 enum FusedStepKind { kFusedPop = 0, kFusedSumFirst = 1, kFusedSumMid = 2, kFusedSumLast = 3 };

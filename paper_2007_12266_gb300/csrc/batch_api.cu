@@ -12,7 +12,7 @@
 #include <vector>
 
 #include "internal.h"
-#include "batch_fused.h"
+#include "batch.h"
 
 using namespace lbm;
 
@@ -29,7 +29,7 @@ struct lbpm_batch {
     DomainView* d_views = nullptr;
     int* d_parity = nullptr;
     std::vector<BatchLaunch> launch[2];          // phase, collide job tables (tile = bt threads)
-    BatchTile* d_mtiles = nullptr;               // measure tiles (256 sites)
+    BatchTile* d_mtiles = nullptr;               // measure tiles (kBatchMeasureTile sites)
     int* d_mbegin = nullptr;                     // [J+1] first measure tile of each job
     double* d_partials = nullptr;
     double* d_out = nullptr;
@@ -151,7 +151,7 @@ lbpm_status rebuild(lbpm_batch* b) {
             ++L.n_jobs;
         }
         mbegin[j] = static_cast<int>(mtiles.size());
-        for (long long f = 0; f < c->N; f += 256) mtiles.push_back(BatchTile{j, static_cast<int>(f)});
+        for (long long f = 0; f < c->N; f += kBatchMeasureTile) mtiles.push_back(BatchTile{j, static_cast<int>(f)});
     }
     mbegin[J] = static_cast<int>(mtiles.size());
     if (!ensure(b, &b->d_views, &b->cap_views, J)) return bfail(b, LBPM_E_OOM, "batch table allocation failed");

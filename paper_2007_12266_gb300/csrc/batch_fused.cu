@@ -19,7 +19,7 @@
 // wrote (populations, sums, phase grid, N, density references) is read with
 // coherent loads; only the static index goes through the read-only path.
 #include "step_kernels.cuh"
-#include "batch_fused.h"
+#include "batch.h"
 
 namespace lbm {
 
