@@ -55,17 +55,21 @@ __global__ void __launch_bounds__(BT) k_batch_phase(const __grid_constant__ Batc
     const int nt = p.tile_begin[p.n_jobs];
     for (int t = blockIdx.x; t < nt; t += gridDim.x) {
         const int j = job_of_tile(p, t);
-        phase_thread<PAR, S>(p.v[j], (t - p.tile_begin[j]) * BT + threadIdx.x);
+        const int i0 = (t - p.tile_begin[j]) * BT * kBatchPhasePer + static_cast<int>(threadIdx.x);
+#pragma unroll
+        for (int k = 0; k < kBatchPhasePer; ++k) phase_thread<PAR, S>(p.v[j], i0 + k * BT);
     }
 }
 
-// Phase pass of the sum form (see phase_sum_thread), one entry per thread.
+// Phase pass of the sum form (see phase_sum_thread), kBatchPhasePer entries
+// per thread.
 template <int PAR, bool WRITE_N, int BT>
 __global__ void __launch_bounds__(BT) k_batch_phase_sum(const __grid_constant__ BatchLaunch p) {
     const int nt = p.tile_begin[p.n_jobs];
     for (int t = blockIdx.x; t < nt; t += gridDim.x) {
         const int j = job_of_tile(p, t);
-        phase_sum_thread<PAR, WRITE_N, 1>(p.v[j], (t - p.tile_begin[j]) * BT + threadIdx.x, BT);
+        phase_sum_thread<PAR, WRITE_N, kBatchPhasePer>(
+            p.v[j], (t - p.tile_begin[j]) * BT * kBatchPhasePer + static_cast<int>(threadIdx.x), BT);
     }
 }
 

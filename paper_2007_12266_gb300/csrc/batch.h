@@ -12,6 +12,12 @@ namespace lbm {
 // the accumulator's 64-site bound).
 constexpr int kBatchMeasureTile = 256 * 32;
 
+// Entries per thread of the batched phase pass (a phase tile holds this many
+// times the threads of a block; two independent round trips in flight per
+// thread, as in the single-domain pass; 2 is 2 % faster than 1 on the 64-job
+// set, 4 the same as 2).
+constexpr int kBatchPhasePer = 2;
+
 // Fused batched form (batch_fused.cu): one cooperative persistent launch per
 // bundle runs the phase pass, the collision and the reservoir reset of every
 // job, with bounded grid barriers between the passes.

@@ -28,7 +28,7 @@ struct lbpm_batch {
     // device tables
     DomainView* d_views = nullptr;
     int* d_parity = nullptr;
-    std::vector<BatchLaunch> launch[2];          // phase, collide job tables (tile = bt threads)
+    std::vector<BatchLaunch> launch[2];          // phase, collide job tables (tile = kBatchPhasePer x bt, bt entries)
     BatchTile* d_mtiles = nullptr;               // measure tiles (kBatchMeasureTile sites)
     int* d_mbegin = nullptr;                     // [J+1] first measure tile of each job
     double* d_partials = nullptr;
@@ -143,7 +143,8 @@ lbpm_status rebuild(lbpm_batch* b) {
                 std::memset(&b->launch[k].back(), 0, sizeof(BatchLaunch));
             }
             BatchLaunch& L = b->launch[k].back();
-            const long long tiles = (counts[k] + b->bt - 1) / b->bt;
+            const long long per_tile = k == 0 ? static_cast<long long>(b->bt) * kBatchPhasePer : b->bt;
+            const long long tiles = (counts[k] + per_tile - 1) / per_tile;
             if (L.tile_begin[L.n_jobs] + tiles > (1LL << 30))
                 return bfail(b, LBPM_E_INVALID, "batch too large for one launch table");
             L.v[L.n_jobs] = views[j];
