@@ -279,7 +279,7 @@ def bench_batched(jobs, precision, steps, device, launch=None):
     for d in doms:
         b.add(d)
     if launch is None:
-        shape = b.tune(steps_per_candidate=4)
+        shape = b.tune(steps_per_candidate=20)
     else:
         b.set_launch(launch[0], launch[1], launch[1])
         shape = (launch[0], launch[1], launch[1])

@@ -383,10 +383,13 @@ lbpm_status lbpm_batch_measure(lbpm_batch* batch, lbpm_measures* out);
  * and -1 for both kernels. */
 lbpm_status lbpm_batch_set_launch(lbpm_batch* batch, int threads, int blocks_per_sm_phase,
                                   int blocks_per_sm_collide);
-/* Autotuner: times each candidate launch shape over steps_per_candidate
- * (even) real steps - all candidates compute identical results - keeps the
- * fastest, and caches it per GPU, precision and size class (log2 of the
- * batch's site count) for the process. Returns the chosen shape. */
+/* Autotuner: times each candidate launch shape over one advance call of
+ * steps_per_candidate (even) real steps - all candidates compute identical
+ * results - keeps the fastest, and caches it per GPU, precision and size
+ * class (log2 of the batch's site count) for the process. Returns the chosen
+ * shape. A call's first and last steps carry the populations and the others
+ * the component sums (lbpm_set_step_form), so a count of 16 or more times
+ * mostly the middle steps that dominate long runs. */
 lbpm_status lbpm_batch_tune(lbpm_batch* batch, int steps_per_candidate, int* threads, int* blocks_per_sm_phase,
                             int* blocks_per_sm_collide);
 /* Kernel launches the batch has issued so far (graph replays counted per

@@ -490,7 +490,9 @@ class Batch:
         self._check(self._L.lbpm_batch_set_launch(self._h, int(threads), int(blocks_per_sm_phase),
                                                   int(blocks_per_sm_collide)))
 
-    def tune(self, steps_per_candidate: int = 4):
+    def tune(self, steps_per_candidate: int = 20):
+        """Time every candidate launch shape over one advance call of
+        steps_per_candidate steps (see lbpm_batch_tune) and keep the fastest."""
         t, p, c = ct.c_int(), ct.c_int(), ct.c_int()
         self._check(self._L.lbpm_batch_tune(self._h, int(steps_per_candidate), ct.byref(t), ct.byref(p),
                                             ct.byref(c)))
