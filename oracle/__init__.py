@@ -16,9 +16,11 @@ Parity status of each oracle function (what pins it, see ``tests/test_oracle_*``
   * full model                      duct Poiseuille series, flat-interface tanh
                                     profile, Laplace law (sigma = 6 alpha),
                                     contact angle cos(theta) = phi_s
-  * reservoir slabs                 parity unpinned (checked: the exact reset
-                                    state after every step, saturation rising
-                                    monotonically, the front advancing)
+  * reservoir slabs                 exact reset state after every step; with
+                                    equal reservoir densities the closed-form
+                                    steady state (rest, linear component
+                                    densities); saturation rising monotonically
+                                    and the front advancing under injection
   * pressure faces, flux inlet      exact face density and zero tangential
                                     momentum, pressure-driven and flux-driven
                                     duct series, uniform component density

@@ -65,11 +65,14 @@
  *     the pressure rho_out.
  *
  * Parity status: every function here is pinned by the tests against closed
- * forms, physics or an independent dense implementation, except the
- * reservoir reset, whose parity is unpinned: the flow it drives has no closed
- * form, and the tests check only that every slab site holds exactly the reset
- * state after each step and that injection raises the saturation
- * monotonically while the displacement front advances. The component
+ * forms, physics or an independent dense implementation. The reservoir reset
+ * is pinned by the exact reset state at every slab site after each step and
+ * by the closed-form steady state it drives when both reservoirs have one
+ * density (rest at that density, component densities exactly linear along a
+ * walled duct between the slabs, with alpha = beta = 0); the pressure-driven
+ * flow between different reservoir densities has no closed form (an entrance
+ * region of the order of the duct width) and is checked for a monotonically
+ * rising saturation and an advancing displacement front. The component
  * population entering at a pressure face (the reservoir fluid's equilibrium at
  * the face velocity) is pinned by a closed form: in a body-force-driven duct
  * between two faces at the same density, the total component density stays

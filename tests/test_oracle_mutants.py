@@ -110,6 +110,15 @@ MUTANTS = [
     ("outlet density in both slabs",
      "const double rho = side == 1 ? o->rho_in : o->rho_out;", "const double rho = o->rho_out;",
      [RES + "test_slab_sites_hold_the_reset_state_after_every_step"]),
+    ("inlet slab one layer thin, seen in the steady state",
+     "if (z < RESERVOIR_DEPTH) side = 1;", "if (z < RESERVOIR_DEPTH - 1) side = 1;",
+     [RES + "test_equal_reservoirs_reach_rest_and_a_linear_component_profile"]),
+    ("inlet slab filled with B as well, seen in the steady state",
+     "B[n * Q7 + q] = side == 1 ? 0.0 : W7[q];", "B[n * Q7 + q] = W7[q];",
+     [RES + "test_equal_reservoirs_reach_rest_and_a_linear_component_profile"]),
+    ("outlet slab filled with A as well",
+     "A[n * Q7 + q] = side == 1 ? W7[q] : 0.0;", "A[n * Q7 + q] = W7[q];",
+     [RES + "test_equal_reservoirs_reach_rest_and_a_linear_component_profile"]),
     ("initial phases of A and B swapped",
      "const double Na = 0.5 * (1.0 + p), Nb = 0.5 * (1.0 - p);",
      "const double Na = 0.5 * (1.0 - p), Nb = 0.5 * (1.0 + p);",
