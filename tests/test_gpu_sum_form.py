@@ -30,6 +30,8 @@ CASES = [
     ("ragged_walls", (0, 1, 0), dict(tau_a=0.9, tau_b=0.6, alpha=0.02, beta=0.7, force=(2e-5, -1e-5, 3e-5))),
     ("closed_box", (0, 0, 0), dict(tau_a=0.55, tau_b=1.4, alpha=0.01, beta=0.95, force=(0.0, 1e-4, 0.0))),
     ("thin_periodic_column", (1, 1, 1), dict(KW)),
+    # reservoir slabs: the reset writes the slab sites' sums inside a call
+    ("reservoir_pack", (1, 1, 0), dict(KW, reservoir_z=1, rho_in=1.001, rho_out=0.999)),
 ]
 
 
@@ -43,6 +45,9 @@ def _case(name):
     if name == "closed_box":
         lab = _pack((6, 11, 5), 0.6, 8)
         return lab, random_affinity(lab, -0.9, 0.9, 9)
+    if name == "reservoir_pack":
+        lab = _pack((16, 8, 10), 0.55, 17)
+        return lab, random_affinity(lab, -0.7, 0.7, 18)
     lab = np.zeros((11, 1, 1), np.uint16)     # x and y neighbours wrap onto the site itself
     return lab, None
 
